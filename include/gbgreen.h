@@ -1,0 +1,195 @@
+/*
+ * gbgreen.h — C ABI of the GB300 shifted Green's-function library.
+ *
+ * The library solves the generalized shifted linear equations
+ *     (z_k S - H) x = b,   b = e_j,
+ * for many complex energy shifts z_k (Im z_k > 0) and many unit right-hand
+ * sides at once, with H a sparse real-symmetric tight-binding Hamiltonian and
+ * S a sparse symmetric positive-definite overlap on the same pattern.  This is
+ * the equation the order-N method of the paper is built on (Introduction:
+ * generalized shifted linear equations used instead of the generalized
+ * eigenproblem H y = lambda S y, cost order N).  The solutions are reduced on
+ * the GPU to Green's-function outputs (local DOS, density-matrix and
+ * energy-density elements on the sparsity pattern, local charge and energy).
+ *
+ * Solver: one seed Krylov space of A = S^{-1} H built by a conjugate
+ * orthogonal CG (COCG) in the S-bilinear form, shared by every shift through
+ * the collinear-residual recurrence; S^{-1} is applied by an inner
+ * block-Jacobi-preconditioned CG.  The paper defers the method's details to
+ * its references; the recurrences used are the standard shifted COCG ones.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GB_OK (0) or a negative gb_status; gb_last_error() gives a
+ *     thread-local message for the last failing call on the calling thread.
+ *   - "host" pointers are read during the call only; "device" pointers are
+ *     CUDA global-memory addresses on the current device, caller-owned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     ordered on that stream.  Calls documented as synchronous wait for their
+ *     own work before returning.
+ *   - The library never frees caller memory and never calls into PyTorch.
+ */
+#ifndef GBGREEN_H
+#define GBGREEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_ABI_VERSION 1
+
+typedef enum {
+  GB_OK = 0,
+  GB_EINVAL = -1,      /* invalid argument (shape, range, NULL, non-finite)   */
+  GB_ENOMEM = -2,      /* device or host allocation failed / workspace small  */
+  GB_ECUDA = -3,       /* a CUDA runtime call failed                          */
+  GB_ENOTSPD = -4,     /* S not positive definite (diagonal block singular, or
+                          the inner CG saw d^T S d <= 0)                      */
+  GB_EBREAKDOWN = -5,  /* COCG breakdown (rho or gamma zero / non-finite) in at
+                          least one column; its outputs are partial           */
+  GB_ENOCONV = -6,     /* at least one (shift, column) pair did not reach tol
+                          within maxit; all outputs are still written and
+                          `converged` tells which pairs met tol              */
+  GB_ETIMEOUT = -7     /* reserved: a bounded device wait gave up             */
+} gb_status;
+
+typedef enum {
+  GB_FP64 = 0,  /* every vector, SpMM and reduction in FP64 */
+  GB_MIXED = 1  /* reduced-precision vector work, FP64 scalars/recurrences */
+} gb_precision;
+
+/* Opaque matrix pair (H, S) resident on one device; library-owned. */
+typedef struct gb_matrix gb_matrix;
+
+typedef struct {
+  int64_t n;          /* basis size (orbitals)                               */
+  int64_t nnz;        /* scalar nonzeros of the shared CSR pattern            */
+  int64_t nb;         /* block rows of the 4x4 BSR (n padded up to 4*nb)      */
+  int64_t nnzb;       /* stored 4x4 blocks                                    */
+  int32_t max_row;    /* longest pattern row (max |R_j|)                      */
+  int32_t block;      /* block size (4)                                       */
+  int32_t device;     /* CUDA device ordinal holding the matrix               */
+  int32_t reserved;
+} gb_matrix_info;
+
+/*
+ * gb_build_bsr — upload (H, S) and build the device block-sparse form.
+ *
+ * The operators of (z S - H) x = b (Introduction).  Input is one CSR pattern
+ * shared by H and S, host memory, caller-owned:
+ *   n        basis size, 1 <= n < 2^31
+ *   row_ptr  [n+1] int64, row_ptr[0] = 0, non-decreasing
+ *   col_idx  [nnz] int32, strictly increasing within each row, 0 <= c < n;
+ *            the pattern must be symmetric and contain every diagonal entry
+ *   h_val, s_val [nnz] float64, finite; both matrices must be symmetric
+ * The CSR is regrouped on the host into 4x4 blocks over the orbital index
+ * (blocks that hold no pattern entry are not stored; padding entries are
+ * zero), copied to the device on `stream`, together with FP32 copies and the
+ * inverses of S's 4x4 diagonal blocks (block-Jacobi preconditioner).
+ * Returns GB_ENOTSPD if a diagonal block of S is not positive definite.
+ * Synchronous.  On success *out owns device memory until gb_free(*out).
+ */
+gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                       const double* h_val, const double* s_val, void* stream,
+                       gb_matrix** out);
+
+/* gb_matrix_get_info — sizes of a built matrix (host struct, caller-owned). */
+gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info);
+
+/* gb_free — release a matrix (NULL is a no-op).  Synchronizes the device. */
+void gb_free(gb_matrix* m);
+
+/*
+ * gb_bsr_to_host — the builder's block form, for inspection and tests.
+ *
+ * Runs the same host regrouping as gb_build_bsr without touching a GPU.
+ * First call with all output pointers NULL to get *nb and *nnzb; then call
+ * again with caller-owned host arrays:
+ *   blk_ptr [nb+1] int32, blk_col [nnzb] int32,
+ *   blk_h, blk_s [nnzb*16] float64 (row-major 4x4 per block).
+ */
+gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                         const double* h_val, const double* s_val, int64_t* nb,
+                         int64_t* nnzb, int32_t* blk_ptr, int32_t* blk_col,
+                         double* blk_h, double* blk_s);
+
+/*
+ * gb_spmm — Y = A X for A = H (which = 0) or S (which = 1).
+ *
+ * The sparse products of the Krylov recurrence (one with H per iteration, one
+ * with S per inner-CG iteration).  X and Y are device arrays of n rows x w
+ * complex columns, row-major with interleaved (re, im): element (i, c) at
+ * [2*(i*w + c)] (re) and [2*(i*w + c) + 1] (im).  prec = GB_FP64: double
+ * arrays and FP64 arithmetic; GB_MIXED: float arrays, FP32 arithmetic with
+ * FP32 accumulation.  1 <= w <= 64.  Asynchronous on `stream`.
+ */
+gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t w,
+                  const void* x, void* y, void* stream);
+
+typedef struct {
+  int32_t nshift;        /* K >= 1                                               */
+  const double* z_re;    /* host [K] real parts of the shifts                   */
+  const double* z_im;    /* host [K] imaginary parts, all > 0                   */
+  const double* w_rho;   /* host [2K] complex weights c^rho_k (re, im pairs), or
+                            NULL: rho / q / e_loc outputs are not formed       */
+  const double* w_edm;   /* host [2K] complex weights c^E_k, or NULL            */
+  int32_t nrhs;          /* number of right-hand sides e_j, >= 1                */
+  const int32_t* rhs_cols; /* host [nrhs] orbital index j of each e_j            */
+  double tol;            /* per-pair target ||b - (z S - H) x|| / ||b|| (> 0)    */
+  int32_t maxit;         /* outer (seed) iteration cap (> 0)                     */
+  gb_precision prec;     /* GB_FP64 or GB_MIXED                                  */
+  double inner_tol;      /* inner-CG relative residual; <= 0: library default
+                            (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level) */
+  int32_t panel;         /* RHS columns per panel (1..32); <= 0: auto            */
+  int32_t cluster;       /* CTAs per team (1, 2, 4, 8, 16); <= 0: auto           */
+  int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
+  int32_t reserved;
+} gb_solve_params;
+
+typedef struct {
+  /* All device pointers, caller-owned; any may be NULL (that output is skipped). */
+  double* ldos;       /* [K][nrhs]  -(1/pi) Im (G(z_k) S)_jj                        */
+  double* rho;        /* [P] packed: for rhs c, entries off[c]..off[c+1]-1 hold
+                         rho_ij = sum_k Im(c^rho_k G_ij(z_k)), i over the pattern
+                         row j in increasing order; off = prefix sums of |R_j|   */
+  double* edm;        /* [P] packed like rho, with the weights c^E_k            */
+  double* q;          /* [nrhs] local charge  sum_i rho_ij S_ij                  */
+  double* e_loc;      /* [nrhs] local energy  sum_i rho_ij H_ij                  */
+  int32_t* iters;     /* [nrhs] seed iterations used                            */
+  uint8_t* converged; /* [K][nrhs] 1 if the pair met tol                        */
+  double* resid;      /* [K][nrhs] recursive residual estimate at exit          */
+  double* g_proj;     /* [K][P][2] optional: G_ij(z_k) (re, im) on the pattern  */
+} gb_outputs;
+
+/*
+ * gb_solve_workspace_size — bytes of device workspace gb_shifted_solve needs
+ * for (m, p).  Returns 0 if the parameters are invalid (see gb_last_error).
+ */
+size_t gb_solve_workspace_size(const gb_matrix* m, const gb_solve_params* p);
+
+/*
+ * gb_shifted_solve — solve (z_k S - H) x = e_j for every shift and RHS, and
+ * reduce the solutions to the outputs in `out` (Introduction: generalized
+ * shifted linear equations).
+ *
+ * `workspace` is caller-owned device memory of at least
+ * gb_solve_workspace_size(m, p) bytes, 256-byte aligned; its contents on entry
+ * are ignored.  One persistent launch processes every panel of RHS columns.
+ * Synchronous: returns after the outputs are written.  GB_ENOCONV and
+ * GB_EBREAKDOWN still write every output.
+ */
+gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* gb_last_error(void);
+
+/* GB_ABI_VERSION of the loaded library. */
+int32_t gb_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBGREEN_H */

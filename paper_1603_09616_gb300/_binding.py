@@ -1,0 +1,289 @@
+"""ctypes binding of ``libgbgreen.so`` (argument marshalling only).
+
+Every step of the shifted Green's-function path runs in the library's CUDA
+kernels; this module only converts PyTorch tensors / NumPy arrays into the
+plain pointers and sizes of the C ABI (``include/gbgreen.h``).  There is no
+CPU fallback: if the library is missing or no CUDA device is present, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbgreen.so")
+
+GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD, GB_EBREAKDOWN, GB_ENOCONV, GB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+GB_FP64, GB_MIXED = 0, 1
+_STATUS = {0: "GB_OK", -1: "GB_EINVAL", -2: "GB_ENOMEM", -3: "GB_ECUDA", -4: "GB_ENOTSPD", -5: "GB_EBREAKDOWN",
+           -6: "GB_ENOCONV", -7: "GB_ETIMEOUT"}
+
+EXPORTED = (
+    "gb_abi_version",
+    "gb_last_error",
+    "gb_bsr_to_host",
+    "gb_build_bsr",
+    "gb_matrix_get_info",
+    "gb_free",
+    "gb_spmm",
+    "gb_solve_workspace_size",
+    "gb_shifted_solve",
+)
+
+
+class GBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MatrixInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64), ("nnzb", C.c_int64),
+                ("max_row", C.c_int32), ("block", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [
+        ("nshift", C.c_int32),
+        ("z_re", C.POINTER(C.c_double)),
+        ("z_im", C.POINTER(C.c_double)),
+        ("w_rho", C.POINTER(C.c_double)),
+        ("w_edm", C.POINTER(C.c_double)),
+        ("nrhs", C.c_int32),
+        ("rhs_cols", C.POINTER(C.c_int32)),
+        ("tol", C.c_double),
+        ("maxit", C.c_int32),
+        ("prec", C.c_int32),
+        ("inner_tol", C.c_double),
+        ("panel", C.c_int32),
+        ("cluster", C.c_int32),
+        ("seed_shift", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class Outputs(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in ("ldos", "rho", "edm", "q", "e_loc", "iters", "converged", "resid", "g_proj")]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    lib.gb_abi_version.restype = C.c_int32
+    lib.gb_last_error.restype = C.c_char_p
+    lib.gb_bsr_to_host.restype = C.c_int
+    lib.gb_bsr_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_build_bsr.restype = C.c_int
+    lib.gb_build_bsr.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]
+    lib.gb_matrix_get_info.restype = C.c_int
+    lib.gb_matrix_get_info.argtypes = [C.c_void_p, C.POINTER(MatrixInfo)]
+    lib.gb_free.restype = None
+    lib.gb_free.argtypes = [C.c_void_p]
+    lib.gb_spmm.restype = C.c_int
+    lib.gb_spmm.argtypes = [C.c_void_p, C.c_int32, C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_solve_workspace_size.restype = C.c_size_t
+    lib.gb_solve_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
+    lib.gb_shifted_solve.restype = C.c_int
+    lib.gb_shifted_solve.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p,
+                                     C.c_size_t, C.c_void_p]
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != GB_OK:
+        raise GBError(st, load().gb_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _csr(system):
+    rp = np.ascontiguousarray(system.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(system.col_idx, dtype=np.int32)
+    hv = np.ascontiguousarray(system.h_val, dtype=np.float64)
+    sv = np.ascontiguousarray(system.s_val, dtype=np.float64)
+    return int(system.n), rp, ci, hv, sv
+
+
+def bsr_to_host(system) -> dict:
+    """The builder's 4x4 block form of (H, S), computed on the host (no GPU)."""
+    lib = load()
+    n, rp, ci, hv, sv = _csr(system)
+    nb, nnzb = C.c_int64(), C.c_int64()
+    _check(lib.gb_bsr_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(nb), C.byref(nnzb),
+                              None, None, None, None))
+    bp = np.zeros(nb.value + 1, np.int32)
+    bc = np.zeros(nnzb.value, np.int32)
+    bh = np.zeros(nnzb.value * 16, np.float64)
+    bs = np.zeros(nnzb.value * 16, np.float64)
+    _check(lib.gb_bsr_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(nb), C.byref(nnzb),
+                              _ptr(bp), _ptr(bc), _ptr(bh), _ptr(bs)))
+    return dict(nb=nb.value, nnzb=nnzb.value, blk_ptr=bp, blk_col=bc, blk_h=bh.reshape(-1, 4, 4),
+                blk_s=bs.reshape(-1, 4, 4))
+
+
+def _stream_handle(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Matrix:
+    """(H, S) resident on the current CUDA device (owns a gb_matrix)."""
+
+    def __init__(self, system, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the library has no CPU path")
+        lib = load()
+        n, rp, ci, hv, sv = _csr(system)
+        h = C.c_void_p()
+        _check(lib.gb_build_bsr(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.system = system
+        info = MatrixInfo()
+        _check(lib.gb_matrix_get_info(h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in MatrixInfo._fields_}
+        self.n = self.info["n"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gb_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spmm(self, which: int, x, prec: str = "fp64", out=None, stream=None):
+        """Y = A X with A = H (which=0) or S (which=1); X complex [n, w] on the GPU."""
+        import torch
+
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        x = x.to(dt).contiguous()
+        assert x.is_cuda and x.dim() == 2 and x.shape[0] == self.n
+        y = out if out is not None else torch.empty_like(x)
+        _check(load().gb_spmm(self._h, int(which), GB_FP64 if prec == "fp64" else GB_MIXED, int(x.shape[1]),
+                              C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), _stream_handle(stream)))
+        return y
+
+
+def pattern_offsets(system, cols) -> np.ndarray:
+    cols = np.asarray(cols, dtype=np.int64)
+    m = system.row_ptr[cols + 1] - system.row_ptr[cols]
+    off = np.zeros(len(cols) + 1, dtype=np.int64)
+    np.cumsum(m, out=off[1:])
+    return off
+
+
+def _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep):
+    z = np.asarray(z, dtype=np.complex128)
+    zr = np.ascontiguousarray(z.real)
+    zi = np.ascontiguousarray(z.imag)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    keep += [zr, zi, cols]
+    p = SolveParams()
+    p.nshift = len(z)
+    p.z_re = zr.ctypes.data_as(C.POINTER(C.c_double))
+    p.z_im = zi.ctypes.data_as(C.POINTER(C.c_double))
+    for name, w in (("w_rho", w_rho), ("w_edm", w_edm)):
+        if w is None:
+            setattr(p, name, C.POINTER(C.c_double)())
+        else:
+            wv = np.ascontiguousarray(np.asarray(w, dtype=np.complex128).view(np.float64))
+            keep.append(wv)
+            setattr(p, name, wv.ctypes.data_as(C.POINTER(C.c_double)))
+    p.nrhs = len(cols)
+    p.rhs_cols = cols.ctypes.data_as(C.POINTER(C.c_int32))
+    p.tol = float(tol)
+    p.maxit = int(maxit)
+    p.prec = GB_FP64 if prec == "fp64" else GB_MIXED
+    p.inner_tol = float(inner_tol)
+    p.panel = int(panel)
+    p.cluster = 0
+    p.seed_shift = int(seed_shift)
+    p.reserved = 0
+    return p
+
+
+def workspace_bytes(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", panel=0) -> int:
+    keep = []
+    p = _params(z, cols, tol, maxit, prec, None, None, 0.0, panel, -1, keep)
+    nb = load().gb_solve_workspace_size(mat.handle, C.byref(p))
+    if nb == 0:
+        raise GBError(GB_EINVAL, load().gb_last_error().decode())
+    return int(nb)
+
+
+def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
+                  inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, workspace=None, stream=None,
+                  raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD)):
+    """Solve (z_k S - H) x = e_j for all shifts and columns; returns device tensors.
+
+    Keys: ldos [K, nrhs], rho / edm [P], q / e_loc [nrhs], iters [nrhs],
+    converged [K, nrhs] (uint8), resid [K, nrhs], g_proj [K, P] complex (if
+    want_g), off [nrhs+1] (host, packed offsets), status (int).
+    """
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    p = _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep)
+    K, nrhs = p.nshift, p.nrhs
+    lib = load()
+    need = lib.gb_solve_workspace_size(mat.handle, C.byref(p))  # validates every parameter
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    off = pattern_offsets(mat.system, cols)
+    P = int(off[-1])
+    f64 = dict(dtype=torch.float64, device=dev)
+    res = dict(
+        ldos=torch.empty((K, nrhs), **f64),
+        rho=torch.empty(P, **f64) if w_rho is not None else None,
+        edm=torch.empty(P, **f64) if w_edm is not None else None,
+        q=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        e_loc=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        converged=torch.empty((K, nrhs), dtype=torch.uint8, device=dev),
+        resid=torch.empty((K, nrhs), **f64),
+        g_proj=torch.empty((K, P), dtype=torch.complex128, device=dev) if want_g else None,
+    )
+    o = Outputs()
+    for f, _ in Outputs._fields_:
+        t = res[f]
+        setattr(o, f, C.c_void_p(t.data_ptr()) if t is not None else None)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    st = lib.gb_shifted_solve(mat.handle, C.byref(p), C.byref(o), C.c_void_p(workspace.data_ptr()),
+                              C.c_size_t(workspace.numel()), _stream_handle(stream))
+    if st in raise_on:
+        _check(st)
+    res["status"] = st
+    res["message"] = lib.gb_last_error().decode()
+    res["off"] = off
+    res["workspace"] = workspace
+    return res

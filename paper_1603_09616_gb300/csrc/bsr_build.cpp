@@ -1,0 +1,151 @@
+// Host side of gb_build_bsr: CSR validation and regrouping into 4x4 blocks.
+//
+// The operators H and S of (z S - H) x = b (Introduction) arrive as one CSR
+// pattern.  The GPU kernels work on 4x4 blocks over the orbital index: a block
+// row covers orbitals 4I..4I+3, a stored block (I, J) holds every pattern entry
+// with row in block row I and column in block column J (missing entries and
+// rows past n are zero).  Carbon atoms (4 orbitals, ordered consecutively and
+// 4-aligned by the generators) fill whole blocks; 1-orbital hydrogens pack
+// four to a block.  The builder also inverts S's diagonal blocks (Cholesky) for
+// the block-Jacobi preconditioner of the inner CG.
+#include "gb_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace gb {
+
+static bool chol4_inverse(const double* a, double* inv) {
+  // a: 4x4 symmetric; returns false unless positive definite.
+  double l[16] = {0};
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = a[i * 4 + j];
+      for (int k = 0; k < j; ++k) s -= l[i * 4 + k] * l[j * 4 + k];
+      if (i == j) {
+        if (!(s > 0.0) || !std::isfinite(s)) return false;
+        l[i * 4 + i] = std::sqrt(s);
+      } else {
+        l[i * 4 + j] = s / l[j * 4 + j];
+      }
+    }
+  }
+  // inverse of L (lower triangular)
+  double li[16] = {0};
+  for (int i = 0; i < 4; ++i) {
+    li[i * 4 + i] = 1.0 / l[i * 4 + i];
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += l[i * 4 + k] * li[k * 4 + j];
+      li[i * 4 + j] = -s / l[i * 4 + i];
+    }
+  }
+  // A^-1 = L^-T L^-1
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = std::max(i, j); k < 4; ++k) s += li[k * 4 + i] * li[k * 4 + j];
+      inv[i * 4 + j] = s;
+    }
+  return true;
+}
+
+gb_status validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
+                       const double* s) {
+  if (n <= 0 || n >= (int64_t(1) << 31)) return fail(GB_EINVAL, "n must be in [1, 2^31)");
+  if (!row_ptr || !col_idx || !h || !s) return fail(GB_EINVAL, "NULL CSR array");
+  if (row_ptr[0] != 0) return fail(GB_EINVAL, "row_ptr[0] must be 0");
+  for (int64_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(GB_EINVAL, "row_ptr must be non-decreasing");
+  const int64_t nnz = row_ptr[n];
+  if (nnz >= (int64_t(1) << 31)) return fail(GB_EINVAL, "nnz must be < 2^31");
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t c = col_idx[e];
+      if (c < 0 || c >= n) return fail(GB_EINVAL, "column index out of range in row %lld", (long long)i);
+      if (e > row_ptr[i] && col_idx[e - 1] >= c)
+        return fail(GB_EINVAL, "columns not strictly increasing in row %lld", (long long)i);
+      if (c == i) diag = true;
+      if (!std::isfinite(h[e]) || !std::isfinite(s[e])) return fail(GB_EINVAL, "non-finite value in row %lld", (long long)i);
+    }
+    if (!diag) return fail(GB_EINVAL, "diagonal entry missing in row %lld", (long long)i);
+  }
+  // symmetry of pattern and values
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col_idx[e];
+      if (j <= i) continue;
+      const int32_t* lo = col_idx + row_ptr[j];
+      const int32_t* hi = col_idx + row_ptr[j + 1];
+      const int32_t* f = std::lower_bound(lo, hi, (int32_t)i);
+      if (f == hi || *f != i) return fail(GB_EINVAL, "pattern not symmetric at (%lld, %d)", (long long)i, j);
+      const int64_t t = f - col_idx;
+      if (h[t] != h[e] || s[t] != s[e]) return fail(GB_EINVAL, "H or S not symmetric at (%lld, %d)", (long long)i, j);
+    }
+  }
+  return GB_OK;
+}
+
+gb_status build_host_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
+                         const double* s, HostBSR* out) {
+  gb_status st = validate_csr(n, row_ptr, col_idx, h, s);
+  if (st != GB_OK) return st;
+  const int64_t nb = (n + 3) / 4;
+  out->n = n;
+  out->nb = nb;
+  out->nnz = row_ptr[n];
+  out->blk_ptr.assign(nb + 1, 0);
+  out->blk_col.clear();
+  std::vector<int32_t> cols;
+  int32_t max_row = 0;
+  for (int64_t i = 0; i < n; ++i) max_row = std::max<int32_t>(max_row, (int32_t)(row_ptr[i + 1] - row_ptr[i]));
+  out->max_row = max_row;
+  for (int64_t I = 0; I < nb; ++I) {
+    cols.clear();
+    for (int64_t i = 4 * I; i < std::min<int64_t>(4 * I + 4, n); ++i)
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) cols.push_back(col_idx[e] / 4);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    out->blk_col.insert(out->blk_col.end(), cols.begin(), cols.end());
+    out->blk_ptr[I + 1] = (int32_t)out->blk_col.size();
+  }
+  const int64_t nnzb = (int64_t)out->blk_col.size();
+  out->nnzb = nnzb;
+  out->blk_h.assign(nnzb * 16, 0.0);
+  out->blk_s.assign(nnzb * 16, 0.0);
+  for (int64_t I = 0; I < nb; ++I) {
+    const int32_t b0 = out->blk_ptr[I], b1 = out->blk_ptr[I + 1];
+    for (int64_t i = 4 * I; i < std::min<int64_t>(4 * I + 4, n); ++i) {
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t J = col_idx[e] / 4;
+        const int32_t* f = std::lower_bound(out->blk_col.data() + b0, out->blk_col.data() + b1, J);
+        const int64_t b = f - out->blk_col.data();
+        const int r = (int)(i - 4 * I), c = col_idx[e] % 4;
+        out->blk_h[b * 16 + r * 4 + c] = h[e];
+        out->blk_s[b * 16 + r * 4 + c] = s[e];
+      }
+    }
+  }
+  // block-Jacobi inverses of S's diagonal blocks (padding rows get a unit diagonal)
+  out->minv.assign(nb * 16, 0.0);
+  for (int64_t I = 0; I < nb; ++I) {
+    const int32_t b0 = out->blk_ptr[I], b1 = out->blk_ptr[I + 1];
+    const int32_t* f = std::lower_bound(out->blk_col.data() + b0, out->blk_col.data() + b1, (int32_t)I);
+    double a[16];
+    std::memcpy(a, out->blk_s.data() + (f - out->blk_col.data()) * 16, sizeof a);
+    for (int r = 0; r < 4; ++r)
+      if (4 * I + r >= n) a[r * 4 + r] = 1.0;
+    if (!chol4_inverse(a, out->minv.data() + I * 16))
+      return fail(GB_ENOTSPD, "diagonal 4x4 block %lld of S is not positive definite", (long long)I);
+  }
+  out->row_ptr.assign(row_ptr, row_ptr + n + 1);
+  out->col_idx.assign(col_idx, col_idx + row_ptr[n]);
+  out->h_val.assign(h, h + row_ptr[n]);
+  out->s_val.assign(s, s + row_ptr[n]);
+  return GB_OK;
+}
+
+}  // namespace gb

@@ -1,0 +1,210 @@
+// Device building blocks of the shifted-COCG team solver.
+//
+// Layout used by every kernel: a panel of W right-hand sides is stored as an
+// N4 x W array (N4 = 4 * block rows, row-major, complex interleaved), element
+// (i, c) at index i * W + c.  A CTA ("team") owns a whole panel; thread t
+// always works on column c = t % W (W divides 32 and the block size), so
+// per-column partial sums stay in one lane position and reduce without
+// atomics, in a fixed order (deterministic results).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ffmath.cuh"
+
+namespace gbk {
+
+constexpr int TPB = 512;
+constexpr int NWARP = TPB / 32;
+constexpr int WMAX = 32;
+constexpr int NVMAX = 4;
+
+struct DevMat {
+  int n, nb;
+  const int* blk_ptr;
+  const int* blk_col;
+  const double* hb;  // FP64 4x4 blocks, row-major inside a block
+  const double* sb;
+  const float* hb_hi;  // float-float split of the same blocks: v = hi + lo
+  const float* hb_lo;
+  const float* sb_hi;
+  const float* sb_lo;
+  const double* minv;  // inverses of S's diagonal blocks (block Jacobi)
+  const float* minv32;
+  const int* row_ptr;  // scalar CSR pattern (for R_j and the reductions)
+  const int* col_idx;
+  const double* h_val;
+  const double* s_val;
+};
+
+// ------------------------------------------------------------ complex FP64
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cinv(double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2(b.x / d, -b.y / d);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return cmul(a, cinv(b)); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ------------------------------------------------------------ block reduce
+struct RedSmem {
+  double red[NWARP * NVMAX * 32];
+  double scal[NVMAX * WMAX];
+};
+
+// Sum NV per-thread partials over all threads sharing column c = tid % W.
+// Result for (value i, column c) lands in rs.scal[i * WMAX + c].  Fixed order.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], int W, RedSmem& rs) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = W; off < 32; off <<= 1) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+  }
+  if (lane < W) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) rs.red[(warp * NV + i) * 32 + lane] = v[i];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NV * W; t += TPB) {
+    const int i = t / W, c = t - i * W;
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += rs.red[(w * NV + i) * 32 + c];
+    rs.scal[i * WMAX + c] = s;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ BSR block-row products
+// acc[r] = sum over stored blocks (I, J) of A_IJ[r][t] * x[4J + t][c]; FP64.
+__device__ __forceinline__ void bsr_row_d(const DevMat& m, const double* __restrict__ A,
+                                          const double2* __restrict__ x, int W, int c, int I,
+                                          double2 (&acc)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_double2(0.0, 0.0);
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I]; b < b1; ++b) {
+    const int J = m.blk_col[b];
+    const double2* xr = x + (size_t)(4 * J) * W + c;
+    double2 xv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = xr[(size_t)t * W];
+    const double2* ab = reinterpret_cast<const double2*>(A + (size_t)b * 16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const double2 a01 = __ldg(ab + 2 * r), a23 = __ldg(ab + 2 * r + 1);
+      acc[r].x = fma(a01.x, xv[0].x, acc[r].x);
+      acc[r].y = fma(a01.x, xv[0].y, acc[r].y);
+      acc[r].x = fma(a01.y, xv[1].x, acc[r].x);
+      acc[r].y = fma(a01.y, xv[1].y, acc[r].y);
+      acc[r].x = fma(a23.x, xv[2].x, acc[r].x);
+      acc[r].y = fma(a23.x, xv[2].y, acc[r].y);
+      acc[r].x = fma(a23.y, xv[3].x, acc[r].x);
+      acc[r].y = fma(a23.y, xv[3].y, acc[r].y);
+    }
+  }
+}
+
+// FP32 matrix (hi part) times FP32 complex vector, FP32 accumulation.
+__device__ __forceinline__ void bsr_row_f(const DevMat& m, const float* __restrict__ A,
+                                          const float2* __restrict__ x, int W, int c, int I,
+                                          float2 (&acc)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_float2(0.f, 0.f);
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I]; b < b1; ++b) {
+    const int J = m.blk_col[b];
+    const float2* xr = x + (size_t)(4 * J) * W + c;
+    float2 xv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = xr[(size_t)t * W];
+    const float4* ab = reinterpret_cast<const float4*>(A + (size_t)b * 16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 a = __ldg(ab + r);
+      acc[r].x = fmaf(a.x, xv[0].x, acc[r].x);
+      acc[r].y = fmaf(a.x, xv[0].y, acc[r].y);
+      acc[r].x = fmaf(a.y, xv[1].x, acc[r].x);
+      acc[r].y = fmaf(a.y, xv[1].y, acc[r].y);
+      acc[r].x = fmaf(a.z, xv[2].x, acc[r].x);
+      acc[r].y = fmaf(a.z, xv[2].y, acc[r].y);
+      acc[r].x = fmaf(a.w, xv[3].x, acc[r].x);
+      acc[r].y = fmaf(a.w, xv[3].y, acc[r].y);
+    }
+  }
+}
+
+// float-float matrix (hi + lo) times float-float complex vector, compensated
+// accumulation: acc_re[r] / acc_im[r] hold the row sums as hi + err.
+__device__ __forceinline__ void bsr_row_ff(const DevMat& m, const float* __restrict__ Ahi,
+                                           const float* __restrict__ Alo, const float4* __restrict__ x,
+                                           int W, int c, int I, gbff::acc (&are)[4], gbff::acc (&aim)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    gbff::acc_init(are[r]);
+    gbff::acc_init(aim[r]);
+  }
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I]; b < b1; ++b) {
+    const int J = m.blk_col[b];
+    const float4* xr = x + (size_t)(4 * J) * W + c;
+    float4 xv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = xr[(size_t)t * W];
+    const float4* ah = reinterpret_cast<const float4*>(Ahi + (size_t)b * 16);
+    const float4* al = reinterpret_cast<const float4*>(Alo + (size_t)b * 16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 h = __ldg(ah + r), l = __ldg(al + r);
+      const float hv[4] = {h.x, h.y, h.z, h.w};
+      const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const gbff::ff a = {hv[t], lv[t]};
+        gbff::acc_mul_add(are[r], a, gbff::ff{xv[t].x, xv[t].y});
+        gbff::acc_mul_add(aim[r], a, gbff::ff{xv[t].z, xv[t].w});
+      }
+    }
+  }
+}
+
+// float-float matrix times FP32 complex vector (x exact in float), compensated.
+__device__ __forceinline__ void bsr_row_ffx(const DevMat& m, const float* __restrict__ Ahi,
+                                            const float* __restrict__ Alo, const float2* __restrict__ x,
+                                            int W, int c, int I, gbff::acc (&are)[4], gbff::acc (&aim)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    gbff::acc_init(are[r]);
+    gbff::acc_init(aim[r]);
+  }
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I]; b < b1; ++b) {
+    const int J = m.blk_col[b];
+    const float2* xr = x + (size_t)(4 * J) * W + c;
+    float2 xv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = xr[(size_t)t * W];
+    const float4* ah = reinterpret_cast<const float4*>(Ahi + (size_t)b * 16);
+    const float4* al = reinterpret_cast<const float4*>(Alo + (size_t)b * 16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 h = __ldg(ah + r), l = __ldg(al + r);
+      const float hv[4] = {h.x, h.y, h.z, h.w};
+      const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const gbff::ff a = {hv[t], lv[t]};
+        gbff::acc_mul_add(are[r], a, xv[t].x);
+        gbff::acc_mul_add(aim[r], a, xv[t].y);
+      }
+    }
+  }
+}
+
+}  // namespace gbk

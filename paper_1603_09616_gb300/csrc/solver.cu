@@ -1,0 +1,480 @@
+// C ABI of the GB300 shifted Green's-function library (declared in gbgreen.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gb_internal.h"
+#include "panel.cuh"
+
+namespace gb {
+
+static thread_local char g_err[512];
+
+gb_status fail(gb_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+void clear_error() { g_err[0] = 0; }
+
+static gb_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(GB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GB_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace gb
+
+struct gb_matrix {
+  int device = 0;
+  int64_t n = 0, nb = 0, nnz = 0, nnzb = 0;
+  int32_t max_row = 0;
+  std::vector<int64_t> h_row_ptr;  // host copy of the pattern's row pointers
+  void* base = nullptr;
+  gbk::DevMat dm{};
+};
+
+using namespace gb;
+
+// ------------------------------------------------------------ standalone SpMM
+namespace {
+
+template <bool F64>
+__global__ void spmm_kernel(const gbk::DevMat m, int which, int W, const void* __restrict__ xv,
+                            void* __restrict__ yv) {
+  const long long items = (long long)m.nb * W;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(it / W), c = (int)(it - (long long)I * W);
+    const int nrow = min(4, m.n - 4 * I);
+    if constexpr (F64) {
+      double2 acc[4];
+      gbk::bsr_row_d(m, which ? m.sb : m.hb, static_cast<const double2*>(xv), W, c, I, acc);
+      double2* y = static_cast<double2*>(yv);
+      for (int r = 0; r < nrow; ++r) y[(size_t)(4 * I + r) * W + c] = acc[r];
+    } else {
+      float2 acc[4];
+      gbk::bsr_row_f(m, which ? m.sb_hi : m.hb_hi, static_cast<const float2*>(xv), W, c, I, acc);
+      float2* y = static_cast<float2*>(yv);
+      for (int r = 0; r < nrow; ++r) y[(size_t)(4 * I + r) * W + c] = acc[r];
+    }
+  }
+}
+
+}  // namespace
+
+// The standalone SpMM reads rows 4J..4J+3 of x for every stored block column
+// J; when n % 4 != 0 the last block column reaches past row n-1 (its matrix
+// entries are zero there), so gb_spmm reads from a zero-padded copy of x.
+
+extern "C" {
+
+int32_t gb_abi_version(void) { return GB_ABI_VERSION; }
+
+const char* gb_last_error(void) { return gb::g_err; }
+
+gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
+                         const double* s_val, int64_t* nb, int64_t* nnzb, int32_t* blk_ptr, int32_t* blk_col,
+                         double* blk_h, double* blk_s) {
+  clear_error();
+  if (!nb || !nnzb) return fail(GB_EINVAL, "nb and nnzb must not be NULL");
+  HostBSR hb;
+  gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
+  if (st != GB_OK) return st;
+  *nb = hb.nb;
+  *nnzb = hb.nnzb;
+  if (blk_ptr) std::memcpy(blk_ptr, hb.blk_ptr.data(), sizeof(int32_t) * hb.blk_ptr.size());
+  if (blk_col) std::memcpy(blk_col, hb.blk_col.data(), sizeof(int32_t) * hb.blk_col.size());
+  if (blk_h) std::memcpy(blk_h, hb.blk_h.data(), sizeof(double) * hb.blk_h.size());
+  if (blk_s) std::memcpy(blk_s, hb.blk_s.data(), sizeof(double) * hb.blk_s.size());
+  return GB_OK;
+}
+
+gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
+                       const double* s_val, void* stream, gb_matrix** out) {
+  clear_error();
+  if (!out) return fail(GB_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  HostBSR hb;
+  gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
+  if (st != GB_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+
+  const size_t nnzb = hb.nnzb, nbl = hb.nb, nnz = hb.nnz;
+  // one allocation, 256-byte aligned pieces
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t o_bp = take(sizeof(int) * (nbl + 1)), o_bc = take(sizeof(int) * nnzb);
+  const size_t o_hb = take(sizeof(double) * nnzb * 16), o_sb = take(sizeof(double) * nnzb * 16);
+  const size_t o_hh = take(sizeof(float) * nnzb * 16), o_hl = take(sizeof(float) * nnzb * 16);
+  const size_t o_sh = take(sizeof(float) * nnzb * 16), o_sl = take(sizeof(float) * nnzb * 16);
+  const size_t o_mi = take(sizeof(double) * nbl * 16), o_m32 = take(sizeof(float) * nbl * 16);
+  const size_t o_rp = take(sizeof(int) * (n + 1)), o_ci = take(sizeof(int) * nnz);
+  const size_t o_hv = take(sizeof(double) * nnz), o_sv = take(sizeof(double) * nnz);
+  const size_t total = off;
+
+  std::vector<char> host(total, 0);
+  auto put = [&](size_t o, const void* src, size_t bytes) { std::memcpy(host.data() + o, src, bytes); };
+  put(o_bp, hb.blk_ptr.data(), sizeof(int) * (nbl + 1));
+  put(o_bc, hb.blk_col.data(), sizeof(int) * nnzb);
+  put(o_hb, hb.blk_h.data(), sizeof(double) * nnzb * 16);
+  put(o_sb, hb.blk_s.data(), sizeof(double) * nnzb * 16);
+  {
+    float* hh = reinterpret_cast<float*>(host.data() + o_hh);
+    float* hl = reinterpret_cast<float*>(host.data() + o_hl);
+    float* sh = reinterpret_cast<float*>(host.data() + o_sh);
+    float* sl = reinterpret_cast<float*>(host.data() + o_sl);
+    for (size_t i = 0; i < nnzb * 16; ++i) {
+      const float a = (float)hb.blk_h[i];
+      hh[i] = a;
+      hl[i] = (float)(hb.blk_h[i] - (double)a);
+      const float b = (float)hb.blk_s[i];
+      sh[i] = b;
+      sl[i] = (float)(hb.blk_s[i] - (double)b);
+    }
+    float* m32 = reinterpret_cast<float*>(host.data() + o_m32);
+    for (size_t i = 0; i < nbl * 16; ++i) m32[i] = (float)hb.minv[i];
+  }
+  put(o_mi, hb.minv.data(), sizeof(double) * nbl * 16);
+  {
+    int* rp = reinterpret_cast<int*>(host.data() + o_rp);
+    for (int64_t i = 0; i <= n; ++i) rp[i] = (int)hb.row_ptr[i];
+  }
+  put(o_ci, hb.col_idx.data(), sizeof(int) * nnz);
+  put(o_hv, hb.h_val.data(), sizeof(double) * nnz);
+  put(o_sv, hb.s_val.data(), sizeof(double) * nnz);
+
+  gb_matrix* m = new gb_matrix();
+  m->device = dev;
+  m->n = n;
+  m->nb = hb.nb;
+  m->nnz = hb.nnz;
+  m->nnzb = hb.nnzb;
+  m->max_row = hb.max_row;
+  m->h_row_ptr = hb.row_ptr;
+  cudaError_t e = cudaMalloc(&m->base, total);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(GB_ENOMEM, "cudaMalloc(%zu bytes) for the matrix failed: %s", total, cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(m->base, host.data(), total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(m->base);
+    delete m;
+    return cuda_fail(e, "matrix upload");
+  }
+  char* b = static_cast<char*>(m->base);
+  gbk::DevMat& d = m->dm;
+  d.n = (int)n;
+  d.nb = (int)hb.nb;
+  d.blk_ptr = reinterpret_cast<const int*>(b + o_bp);
+  d.blk_col = reinterpret_cast<const int*>(b + o_bc);
+  d.hb = reinterpret_cast<const double*>(b + o_hb);
+  d.sb = reinterpret_cast<const double*>(b + o_sb);
+  d.hb_hi = reinterpret_cast<const float*>(b + o_hh);
+  d.hb_lo = reinterpret_cast<const float*>(b + o_hl);
+  d.sb_hi = reinterpret_cast<const float*>(b + o_sh);
+  d.sb_lo = reinterpret_cast<const float*>(b + o_sl);
+  d.minv = reinterpret_cast<const double*>(b + o_mi);
+  d.minv32 = reinterpret_cast<const float*>(b + o_m32);
+  d.row_ptr = reinterpret_cast<const int*>(b + o_rp);
+  d.col_idx = reinterpret_cast<const int*>(b + o_ci);
+  d.h_val = reinterpret_cast<const double*>(b + o_hv);
+  d.s_val = reinterpret_cast<const double*>(b + o_sv);
+  *out = m;
+  return GB_OK;
+}
+
+gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info) {
+  clear_error();
+  if (!m || !info) return fail(GB_EINVAL, "NULL argument");
+  info->n = m->n;
+  info->nnz = m->nnz;
+  info->nb = m->nb;
+  info->nnzb = m->nnzb;
+  info->max_row = m->max_row;
+  info->block = 4;
+  info->device = m->device;
+  info->reserved = 0;
+  return GB_OK;
+}
+
+void gb_free(gb_matrix* m) {
+  if (!m) return;
+  if (m->base) {
+    cudaDeviceSynchronize();
+    cudaFree(m->base);
+  }
+  delete m;
+}
+
+gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t w, const void* x, void* y,
+                  void* stream) {
+  clear_error();
+  if (!m || !x || !y) return fail(GB_EINVAL, "NULL argument");
+  if (which != 0 && which != 1) return fail(GB_EINVAL, "which must be 0 (H) or 1 (S)");
+  if (w < 1 || w > 64) return fail(GB_EINVAL, "w must be in [1, 64]");
+  if (prec != GB_FP64 && prec != GB_MIXED) return fail(GB_EINVAL, "bad precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t esz = prec == GB_FP64 ? 16 : 8;
+  const int64_t n4 = 4 * m->nb;
+  const void* xin = x;
+  void* pad = nullptr;
+  if (n4 != m->n) {  // last block column reads rows up to 4*nb - 1: pad x with zero rows
+    GB_CUDA(cudaMallocAsync(&pad, esz * n4 * w, s));
+    GB_CUDA(cudaMemsetAsync(pad, 0, esz * n4 * w, s));
+    GB_CUDA(cudaMemcpyAsync(pad, x, esz * m->n * w, cudaMemcpyDeviceToDevice, s));
+    xin = pad;
+  }
+  const long long items = (long long)m->nb * w;
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>((items + threads - 1) / threads, 152LL * 32);
+  if (prec == GB_FP64)
+    spmm_kernel<true><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
+  else
+    spmm_kernel<false><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
+  cudaError_t e = cudaGetLastError();
+  if (pad) cudaFreeAsync(pad, s);
+  if (e != cudaSuccess) return cuda_fail(e, "spmm launch");
+  return GB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ shifted solve
+namespace {
+
+struct Plan {
+  int W, KG, npanels, teams, Mcap, inner_maxit;
+  double itol;
+  size_t team_bytes, header_bytes, total;
+  size_t o_z, o_wr, o_we, o_cols, o_off, o_status, o_counter;
+  gbk::Args a;
+};
+
+gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, Plan* pl) {
+  if (!m) return fail(GB_EINVAL, "matrix is NULL");
+  if (!p) return fail(GB_EINVAL, "params is NULL");
+  if (p->nshift < 1 || p->nshift > 256) return fail(GB_EINVAL, "nshift must be in [1, 256]");
+  if (!p->z_re || !p->z_im) return fail(GB_EINVAL, "shift arrays are NULL");
+  for (int k = 0; k < p->nshift; ++k)
+    if (!std::isfinite(p->z_re[k]) || !std::isfinite(p->z_im[k]) || !(p->z_im[k] > 0.0))
+      return fail(GB_EINVAL, "shift %d must be finite with Im z > 0", k);
+  if (p->nrhs < 1 || !p->rhs_cols) return fail(GB_EINVAL, "need nrhs >= 1 and rhs_cols");
+  for (int i = 0; i < p->nrhs; ++i)
+    if (p->rhs_cols[i] < 0 || p->rhs_cols[i] >= m->n) return fail(GB_EINVAL, "rhs_cols[%d] out of range", i);
+  if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(GB_EINVAL, "tol must be > 0");
+  if (p->maxit < 1 || p->maxit > 1000000) return fail(GB_EINVAL, "maxit must be in [1, 1e6]");
+  if (p->prec != GB_FP64 && p->prec != GB_MIXED) return fail(GB_EINVAL, "bad precision");
+  if (p->seed_shift >= p->nshift) return fail(GB_EINVAL, "seed_shift out of range");
+  const double* ws[2] = {p->w_rho, p->w_edm};
+  for (int q = 0; q < 2; ++q)
+    if (ws[q])
+      for (int k = 0; k < 2 * p->nshift; ++k)
+        if (!std::isfinite(ws[q][k])) return fail(GB_EINVAL, "non-finite quadrature weight");
+
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, m->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  const int nsm = prop.multiProcessorCount;
+
+  int W = p->panel;
+  if (W <= 0) {
+    W = 1;
+    for (int cand : {32, 16, 8, 4, 2}) {
+      if ((p->nrhs + cand - 1) / cand >= nsm) {
+        W = cand;
+        break;
+      }
+    }
+  }
+  if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32)
+    return fail(GB_EINVAL, "panel must be 1, 2, 4, 8, 16 or 32");
+  pl->W = W;
+  pl->KG = (p->nshift + 31) / 32;
+  pl->npanels = (p->nrhs + W - 1) / W;
+  pl->teams = std::min(pl->npanels, nsm);
+  pl->Mcap = W * m->max_row;
+  pl->inner_maxit = 500;
+  // Inner-solve accuracy: the seed recurrence treats w = S^{-1} H p as exact,
+  // and each iteration's error enters the shifted residual gap, so the inner
+  // solve runs close to working precision (FP64: 1e-14; mixed: 1e-7 per FP32
+  // refinement level, ~1e-14 after the float-float residual step).
+  if (p->prec == GB_FP64)
+    pl->itol = p->inner_tol > 0 ? p->inner_tol : 1e-14;
+  else
+    pl->itol = p->inner_tol > 0 ? p->inner_tol : 1e-7;
+
+  const size_t K = p->nshift, Wz = W, maxit = p->maxit, N4 = 4 * (size_t)m->nb;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  gbk::Args& a = pl->a;
+  std::memset(&a, 0, sizeof a);
+  const size_t vec = N4 * Wz * 16;
+  a.o_r = take(vec);
+  a.o_rt = take(vec);
+  a.o_p = take(vec);
+  a.o_sp = take(vec);
+  a.o_u = take(vec);
+  a.o_w = take(vec);
+  a.o_g = take(vec);
+  a.o_d = take(vec);
+  a.o_q = take(vec);
+  a.o_x = take(vec);
+  a.o_hr = take((maxit + 1) * (size_t)pl->Mcap * 16);
+  a.o_ab = take(maxit * Wz * 2 * 16);
+  a.o_L = take((maxit + 1) * Wz * sizeof(int));
+  a.o_t = take((maxit + 1) * Wz * 16);
+  a.o_ck = take((maxit / gbk::CK + 1) * Wz * K * 2 * 16);
+  a.o_pi = take(Wz * K * 2 * 16);
+  a.o_nk = take(Wz * K * sizeof(int));
+  a.o_res = take(Wz * K * sizeof(double));
+  a.o_buf = take((gbk::CK + 1) * Wz * K * 16);
+  a.o_cp = take((maxit + 1) * Wz * pl->KG * 2 * 16);
+  a.o_cf = take((maxit + 1) * Wz * 2 * 16);
+  a.o_cg = want_g ? take((maxit + 1) * Wz * K * 16) : 0;
+  pl->team_bytes = off;
+
+  off = 0;
+  pl->o_z = take(K * 16);
+  pl->o_wr = take(K * 16);
+  pl->o_we = take(K * 16);
+  pl->o_cols = take(sizeof(int) * p->nrhs);
+  pl->o_off = take(sizeof(long long) * (p->nrhs + 1));
+  pl->o_status = take(sizeof(int) * p->nrhs);
+  pl->o_counter = take(sizeof(int));
+  pl->header_bytes = off;
+  pl->total = pl->header_bytes + pl->team_bytes * pl->teams + 256;
+  return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_solve_workspace_size(const gb_matrix* m, const gb_solve_params* p) {
+  clear_error();
+  Plan pl;
+  if (make_plan(m, p, true, &pl) != GB_OK) return 0;
+  return pl.total;
+}
+
+gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!out) return fail(GB_EINVAL, "outputs is NULL");
+  Plan pl;
+  const bool want_g = out->g_proj != nullptr;
+  gb_status st = make_plan(m, p, want_g, &pl);
+  if (st != GB_OK) return st;
+  if (!workspace) return fail(GB_EINVAL, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(GB_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < pl.total)
+    return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, pl.total);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device %d differs from the matrix's device %d", dev, m->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  const int K = p->nshift, nrhs = p->nrhs;
+  // packed output offsets: prefix sums of |R_j|
+  std::vector<char> hdr(pl.header_bytes, 0);
+  double2* hz = reinterpret_cast<double2*>(hdr.data() + pl.o_z);
+  double2* hwr = reinterpret_cast<double2*>(hdr.data() + pl.o_wr);
+  double2* hwe = reinterpret_cast<double2*>(hdr.data() + pl.o_we);
+  for (int k = 0; k < K; ++k) {
+    hz[k] = make_double2(p->z_re[k], p->z_im[k]);
+    hwr[k] = p->w_rho ? make_double2(p->w_rho[2 * k], p->w_rho[2 * k + 1]) : make_double2(0, 0);
+    hwe[k] = p->w_edm ? make_double2(p->w_edm[2 * k], p->w_edm[2 * k + 1]) : make_double2(0, 0);
+  }
+  std::memcpy(hdr.data() + pl.o_cols, p->rhs_cols, sizeof(int) * nrhs);
+  const std::vector<int64_t>& rp = m->h_row_ptr;
+  long long* ho = reinterpret_cast<long long*>(hdr.data() + pl.o_off);
+  ho[0] = 0;
+  for (int i = 0; i < nrhs; ++i) {
+    const int j = p->rhs_cols[i];
+    ho[i + 1] = ho[i] + (rp[j + 1] - rp[j]);
+  }
+  char* wsb = static_cast<char*>(workspace);
+  GB_CUDA(cudaMemcpyAsync(wsb, hdr.data(), pl.header_bytes, cudaMemcpyHostToDevice, s));
+
+  gbk::Args& a = pl.a;
+  a.m = m->dm;
+  a.K = K;
+  a.W = pl.W;
+  a.KG = pl.KG;
+  a.nrhs = nrhs;
+  a.npanels = pl.npanels;
+  a.maxit = p->maxit;
+  a.inner_maxit = pl.inner_maxit;
+  a.has_rho = p->w_rho != nullptr;
+  a.has_edm = p->w_edm != nullptr;
+  a.want_g = want_g;
+  a.tol = p->tol;
+  a.itol = pl.itol;
+  const int seed = p->seed_shift >= 0 ? p->seed_shift : K / 2;
+  a.sigma = make_double2(p->z_re[seed], p->z_im[seed]);
+  a.z = reinterpret_cast<const double2*>(wsb + pl.o_z);
+  a.w_rho = reinterpret_cast<const double2*>(wsb + pl.o_wr);
+  a.w_edm = reinterpret_cast<const double2*>(wsb + pl.o_we);
+  a.rhs_cols = reinterpret_cast<const int*>(wsb + pl.o_cols);
+  a.out_off = reinterpret_cast<const long long*>(wsb + pl.o_off);
+  a.status = reinterpret_cast<int*>(wsb + pl.o_status);
+  a.panel_counter = reinterpret_cast<int*>(wsb + pl.o_counter);
+  a.team_ws = wsb + align256(pl.header_bytes);
+  a.team_bytes = pl.team_bytes;
+  a.Mcap = pl.Mcap;
+  a.ldos = out->ldos;
+  a.rho = out->rho;
+  a.edm = out->edm;
+  a.q = out->q;
+  a.e_loc = out->e_loc;
+  a.iters = out->iters;
+  a.conv = out->converged;
+  a.resid = out->resid;
+  a.g_proj = reinterpret_cast<double2*>(out->g_proj);
+  a.P = ho[nrhs];
+
+  if (p->prec == GB_FP64)
+    gbk::team_kernel<false><<<pl.teams, gbk::TPB, 0, s>>>(a);
+  else
+    gbk::team_kernel<true><<<pl.teams, gbk::TPB, 0, s>>>(a);
+  GB_CUDA(cudaGetLastError());
+  std::vector<int> hst(nrhs);
+  GB_CUDA(cudaMemcpyAsync(hst.data(), a.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  int any = 0;
+  for (int v : hst) any |= v;
+  if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
+  if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
+  if (any & (gbk::kStNoConv | gbk::kStInner))
+    return fail(GB_ENOCONV, "some (shift, column) pairs did not reach tol within maxit%s",
+                (any & gbk::kStInner) ? " (inner CG hit its cap)" : "");
+  return GB_OK;
+}
+
+}  // extern "C"

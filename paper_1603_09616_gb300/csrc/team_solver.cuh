@@ -1,0 +1,461 @@
+// Persistent team solver: shifted COCG in the S-bilinear form for a panel of
+// W unit right-hand sides, all shifts at once, plus the Green's-function
+// reductions.  One CTA is one team; teams pull panels from a device counter.
+//
+// Method (Introduction: generalized shifted linear equations (z S - H) x = b).
+// With A = S^{-1} H the equations read (z I - A) x = S^{-1} b.  A is
+// self-adjoint in the bilinear form <u, v> = u^T S v, so one COCG run for a
+// seed shift sigma builds a Krylov space shared by every shift z_k (shift
+// invariance) and the shifted residuals stay collinear, r^k_n = r_n / pi^k_n.
+// Seed recurrence (rt = S r is carried instead of recomputed):
+//   U = H p,  w = S^{-1} U                 (inner CG)
+//   gamma = sigma (S p)^T p - p^T U,  alpha = rho / gamma
+//   rt <- rt - alpha (sigma S p - U),  r <- r - alpha (sigma p - w)
+//   beta = rho' / rho,  p <- r + beta p,  S p <- rt + beta S p
+// Shift polynomials (delta_k = z_k - sigma, alpha_{-1} = 1, beta_{-1} = 0):
+//   pi_{n+1} = (1 + alpha_n delta_k) pi_n + (alpha_n beta_{n-1}/alpha_{n-1}) (pi_n - pi_{n-1})
+// Shift k has converged at n_k when ||rt_n|| / |pi^k_n| <= tol (= the true
+// residual ||b - (z_k S - H) x^k|| for ||b|| = 1, since b - (zS-H)x = S r^k).
+//
+// Projected solutions without per-shift vector updates.  The shifted iterate
+// x^k = sum_{n<n_k} alpha^k_n p^k_n, p^k_{n+1} = r_{n+1}/pi^k_{n+1} + beta^k_n p^k_n,
+// alpha^k_n = (pi_n/pi_{n+1}) alpha_n, beta^k_n = (pi_n/pi_{n+1})^2 beta_n, is
+// rewritten as x^k = sum_m c^k_m r_m with c^k_m = S^k_m / pi^k_m and the
+// backward recurrence S^k_m = alpha^k_m + beta^k_m S^k_{m+1}, S^k_{n_k} = 0.
+// Every output is a linear functional of x^k restricted to the rows R_j of the
+// pattern, so the loop only records r_m[R_j] and the seed scalars; the final
+// phase replays the pi recurrence from checkpoints and contracts.  This costs
+// O(K) FP64 scalar work per iteration instead of O(K |R_j|) vector work.
+#pragma once
+#include "kernels.cuh"
+
+namespace gbk {
+
+constexpr int CK = 64;                      // checkpoint interval of the pi recurrence
+constexpr double kRescaleBelow2 = 0x1p-64;  // rescale seed vectors when ||rt||^2 < 2^-64
+constexpr int kRescaleExp = 32;             // ... by 2^32 (exact)
+
+struct Args {
+  DevMat m;
+  int K, W, KG, nrhs, npanels, maxit, inner_maxit, has_rho, has_edm, want_g;
+  double tol, itol;
+  double2 sigma;
+  const double2* z;
+  const double2* w_rho;
+  const double2* w_edm;
+  const int* rhs_cols;
+  const long long* out_off;
+  int* panel_counter;
+  int* status;  // [nrhs] bit flags, see kSt*
+  char* team_ws;
+  size_t team_bytes;
+  size_t o_r, o_rt, o_p, o_sp, o_u, o_w, o_g, o_d, o_q, o_x;
+  size_t o_hr, o_ab, o_L, o_t, o_ck, o_pi, o_nk, o_res, o_buf, o_cp, o_cf, o_cg;
+  int Mcap;
+  double* ldos;
+  double* rho;
+  double* edm;
+  double* q;
+  double* e_loc;
+  int* iters;
+  unsigned char* conv;
+  double* resid;
+  double2* g_proj;
+  long long P;
+};
+
+constexpr int kStBreakdown = 1;
+constexpr int kStNotSPD = 2;
+constexpr int kStNoConv = 4;
+constexpr int kStInner = 8;
+
+struct Smem {
+  RedSmem rs;
+  int panel, Wp, flag;
+  int j[WMAX], mc[WMAX], off[WMAX + 1], act[WMAX], nc[WMAX], nact[WMAX], st[WMAX];
+  double2 rho[WMAX], alpha[WMAX], beta[WMAX], aprev[WMAX], bprev[WMAX], gam[WMAX];
+  double rt2[WMAX], scl[WMAX];
+  double cg_rho[2 * WMAX], cg_un[2 * WMAX], cg_gg[2 * WMAX], cg_a[2 * WMAX], cg_b[2 * WMAX];
+};
+
+template <typename T>
+__device__ __forceinline__ T* wsp(char* ws, size_t off) {
+  return reinterpret_cast<T*>(ws + off);
+}
+
+// The same routine advances the pi recurrence in the loop and in the final
+// replay, so both produce identical values.
+__device__ __noinline__ double2 shift_coef(double2 a_n, double2 b_prev, double2 a_prev) {
+  return cdiv(cmul(a_n, b_prev), a_prev);
+}
+__device__ __noinline__ double2 pi_step(double2 cur, double2 prev, double2 a_n, double2 coef, double2 delta) {
+  double2 ad = cmul(a_n, delta);
+  ad.x += 1.0;
+  const double2 t = cmul(ad, cur);
+  const double2 u = cmul(coef, csub(cur, prev));
+  return cadd(t, u);
+}
+
+// ------------------------------------------------------------ inner CG, FP64
+// Solves S x = f per real column (re, im parts separately), block-Jacobi
+// preconditioned, zero initial guess, until ||g|| <= itol ||f|| for every
+// active real column.
+__device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, double2* g, double2* d,
+                     double2* q) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  {
+    double v[4] = {0, 0, 0, 0};
+    for (int it = threadIdx.x; it < nb * W; it += TPB) {
+      if (!sm.act[c]) continue;
+      const int I = it / W;
+      double2 gv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) gv[r] = f[(size_t)(4 * I + r) * W + c];
+      const double* Mi = a.m.minv + (size_t)I * 16;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        double2 zr = make_double2(0, 0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          zr.x = fma(Mi[r * 4 + t], gv[t].x, zr.x);
+          zr.y = fma(Mi[r * 4 + t], gv[t].y, zr.y);
+        }
+        const size_t e = (size_t)(4 * I + r) * W + c;
+        g[e] = gv[r];
+        d[e] = zr;
+        x[e] = make_double2(0, 0);
+        v[0] = fma(gv[r].x, zr.x, v[0]);
+        v[1] = fma(gv[r].y, zr.y, v[1]);
+        v[2] = fma(gv[r].x, gv[r].x, v[2]);
+        v[3] = fma(gv[r].y, gv[r].y, v[3]);
+      }
+    }
+    block_reduce<4>(v, W, sm.rs);
+    if (threadIdx.x < 2 * W) {
+      const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+      sm.cg_rho[threadIdx.x] = sm.rs.scal[p * WMAX + cc];
+      sm.cg_un[threadIdx.x] = sm.rs.scal[(2 + p) * WMAX + cc];
+      sm.cg_gg[threadIdx.x] = sm.cg_un[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  const double it2 = a.itol * a.itol;
+  for (int iter = 0;; ++iter) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < 2 * W; ++k)
+        if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = 0;
+      if (!done && iter >= a.inner_maxit) {
+        done = 1;
+        for (int k = 0; k < W; ++k)
+          if (sm.act[k]) sm.st[k] |= kStInner;
+      }
+      sm.flag = done;
+    }
+    __syncthreads();
+    if (sm.flag) break;
+    {  // q = S d, d^T q
+      double v[2] = {0, 0};
+      for (int it = threadIdx.x; it < nb * W; it += TPB) {
+        if (!sm.act[c]) continue;
+        const int I = it / W;
+        double2 acc[4];
+        bsr_row_d(a.m, a.m.sb, d, W, c, I, acc);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const size_t e = (size_t)(4 * I + r) * W + c;
+          const double2 dv = d[e];
+          q[e] = acc[r];
+          v[0] = fma(dv.x, acc[r].x, v[0]);
+          v[1] = fma(dv.y, acc[r].y, v[1]);
+        }
+      }
+      block_reduce<2>(v, W, sm.rs);
+      if (threadIdx.x < 2 * W) {
+        const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+        const double dq = sm.rs.scal[p * WMAX + cc];
+        double al = 0.0;
+        if (dq > 0.0) al = sm.cg_rho[threadIdx.x] / dq;
+        else if (dq < 0.0 && sm.act[cc]) sm.st[cc] |= kStNotSPD;
+        sm.cg_a[threadIdx.x] = al;
+      }
+      __syncthreads();
+    }
+    {  // x += a d, g -= a q, z = M^-1 g (into q), g^T z, g^T g
+      double v[4] = {0, 0, 0, 0};
+      for (int it = threadIdx.x; it < nb * W; it += TPB) {
+        if (!sm.act[c]) continue;
+        const int I = it / W;
+        const double ar = sm.cg_a[2 * c], ai = sm.cg_a[2 * c + 1];
+        double2 gv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const size_t e = (size_t)(4 * I + r) * W + c;
+          const double2 dv = d[e], qv = q[e];
+          double2 xv = x[e];
+          xv.x = fma(ar, dv.x, xv.x);
+          xv.y = fma(ai, dv.y, xv.y);
+          x[e] = xv;
+          double2 gg = g[e];
+          gg.x = fma(-ar, qv.x, gg.x);
+          gg.y = fma(-ai, qv.y, gg.y);
+          g[e] = gg;
+          gv[r] = gg;
+        }
+        const double* Mi = a.m.minv + (size_t)I * 16;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          double2 zr = make_double2(0, 0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            zr.x = fma(Mi[r * 4 + t], gv[t].x, zr.x);
+            zr.y = fma(Mi[r * 4 + t], gv[t].y, zr.y);
+          }
+          q[(size_t)(4 * I + r) * W + c] = zr;
+          v[0] = fma(gv[r].x, zr.x, v[0]);
+          v[1] = fma(gv[r].y, zr.y, v[1]);
+          v[2] = fma(gv[r].x, gv[r].x, v[2]);
+          v[3] = fma(gv[r].y, gv[r].y, v[3]);
+        }
+      }
+      block_reduce<4>(v, W, sm.rs);
+      if (threadIdx.x < 2 * W) {
+        const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+        const double rn = sm.rs.scal[p * WMAX + cc];
+        const double ro = sm.cg_rho[threadIdx.x];
+        sm.cg_b[threadIdx.x] = (ro != 0.0) ? rn / ro : 0.0;
+        sm.cg_rho[threadIdx.x] = rn;
+        sm.cg_gg[threadIdx.x] = sm.rs.scal[(2 + p) * WMAX + cc];
+      }
+      __syncthreads();
+    }
+    // d = z + b d
+    for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+      if (!sm.act[c]) continue;
+      const double br = sm.cg_b[2 * c], bi = sm.cg_b[2 * c + 1];
+      const double2 zv = q[e];
+      double2 dv = d[e];
+      dv.x = fma(br, dv.x, zv.x);
+      dv.y = fma(bi, dv.y, zv.y);
+      d[e] = dv;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ inner CG, FP32 loop
+// Runs on (x, g, d) already initialised (x = 0, g = rhs, d = M^-1 g) with
+// cg_rho / cg_un / cg_gg set.  FP32 vectors, FP64 scalars.
+__device__ void cg32_loop(const Args& a, Smem& sm, float2* x, float2* g, float2* d, float2* q, double itol) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  const double it2 = itol * itol;
+  for (int iter = 0;; ++iter) {
+    if (threadIdx.x == 0) {
+      int done = 1;
+      for (int k = 0; k < 2 * W; ++k)
+        if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = 0;
+      if (!done && iter >= a.inner_maxit) {
+        done = 1;
+        for (int k = 0; k < W; ++k)
+          if (sm.act[k]) sm.st[k] |= kStInner;
+      }
+      sm.flag = done;
+    }
+    __syncthreads();
+    if (sm.flag) break;
+    {
+      double v[2] = {0, 0};
+      float v0 = 0.f, v1 = 0.f;
+      for (int it = threadIdx.x; it < nb * W; it += TPB) {
+        if (!sm.act[c]) continue;
+        const int I = it / W;
+        float2 acc[4];
+        bsr_row_f(a.m, a.m.sb_hi, d, W, c, I, acc);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const size_t e = (size_t)(4 * I + r) * W + c;
+          const float2 dv = d[e];
+          q[e] = acc[r];
+          v0 = fmaf(dv.x, acc[r].x, v0);
+          v1 = fmaf(dv.y, acc[r].y, v1);
+        }
+      }
+      v[0] = v0;
+      v[1] = v1;
+      block_reduce<2>(v, W, sm.rs);
+      if (threadIdx.x < 2 * W) {
+        const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+        const double dq = sm.rs.scal[p * WMAX + cc];
+        double al = 0.0;
+        if (dq > 0.0) al = sm.cg_rho[threadIdx.x] / dq;
+        else if (dq < 0.0 && sm.act[cc]) sm.st[cc] |= kStNotSPD;
+        sm.cg_a[threadIdx.x] = al;
+      }
+      __syncthreads();
+    }
+    {
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+      for (int it = threadIdx.x; it < nb * W; it += TPB) {
+        if (!sm.act[c]) continue;
+        const int I = it / W;
+        const float ar = (float)sm.cg_a[2 * c], ai = (float)sm.cg_a[2 * c + 1];
+        float2 gv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const size_t e = (size_t)(4 * I + r) * W + c;
+          const float2 dv = d[e], qv = q[e];
+          float2 xv = x[e];
+          xv.x = fmaf(ar, dv.x, xv.x);
+          xv.y = fmaf(ai, dv.y, xv.y);
+          x[e] = xv;
+          float2 gg = g[e];
+          gg.x = fmaf(-ar, qv.x, gg.x);
+          gg.y = fmaf(-ai, qv.y, gg.y);
+          g[e] = gg;
+          gv[r] = gg;
+        }
+        const float4* Mi = reinterpret_cast<const float4*>(a.m.minv32 + (size_t)I * 16);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 mr = __ldg(Mi + r);
+          float2 zr;
+          zr.x = mr.x * gv[0].x + mr.y * gv[1].x + mr.z * gv[2].x + mr.w * gv[3].x;
+          zr.y = mr.x * gv[0].y + mr.y * gv[1].y + mr.z * gv[2].y + mr.w * gv[3].y;
+          q[(size_t)(4 * I + r) * W + c] = zr;
+          f0 = fmaf(gv[r].x, zr.x, f0);
+          f1 = fmaf(gv[r].y, zr.y, f1);
+          f2 = fmaf(gv[r].x, gv[r].x, f2);
+          f3 = fmaf(gv[r].y, gv[r].y, f3);
+        }
+      }
+      double v[4] = {f0, f1, f2, f3};
+      block_reduce<4>(v, W, sm.rs);
+      if (threadIdx.x < 2 * W) {
+        const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+        const double rn = sm.rs.scal[p * WMAX + cc];
+        const double ro = sm.cg_rho[threadIdx.x];
+        sm.cg_b[threadIdx.x] = (ro != 0.0) ? rn / ro : 0.0;
+        sm.cg_rho[threadIdx.x] = rn;
+        sm.cg_gg[threadIdx.x] = sm.rs.scal[(2 + p) * WMAX + cc];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+      if (!sm.act[c]) continue;
+      const float br = (float)sm.cg_b[2 * c], bi = (float)sm.cg_b[2 * c + 1];
+      const float2 zv = q[e];
+      float2 dv = d[e];
+      dv.x = fmaf(br, dv.x, zv.x);
+      dv.y = fmaf(bi, dv.y, zv.y);
+      d[e] = dv;
+    }
+    __syncthreads();
+  }
+}
+
+// Stores the per-real-column CG start scalars from a reduced {g^T z, ||f||^2}.
+__device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
+  if (threadIdx.x < 2 * W) {
+    const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
+    sm.cg_rho[threadIdx.x] = sm.rs.scal[p * WMAX + cc];
+    sm.cg_un[threadIdx.x] = sm.rs.scal[(2 + p) * WMAX + cc];
+    sm.cg_gg[threadIdx.x] = sm.cg_un[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ inner solve, mixed
+// w = S^{-1} U to ~FP64 accuracy: FP32 CG on hi(U), a float-float residual
+// e = U - S x1, FP32 CG on e, w = x1 + x2 (float-float).
+__device__ void inner_mixed(const Args& a, Smem& sm, const float4* U, float4* w, float2* x, float2* g,
+                            float2* d, float2* q) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  const double itol = a.itol;
+  {  // level 1 start: g = hi(U), d = M^-1 g, x = 0
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    for (int it = threadIdx.x; it < nb * W; it += TPB) {
+      if (!sm.act[c]) continue;
+      const int I = it / W;
+      float2 gv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 u = U[(size_t)(4 * I + r) * W + c];
+        gv[r] = make_float2(u.x, u.z);
+      }
+      const float4* Mi = reinterpret_cast<const float4*>(a.m.minv32 + (size_t)I * 16);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 mr = __ldg(Mi + r);
+        float2 zr;
+        zr.x = mr.x * gv[0].x + mr.y * gv[1].x + mr.z * gv[2].x + mr.w * gv[3].x;
+        zr.y = mr.x * gv[0].y + mr.y * gv[1].y + mr.z * gv[2].y + mr.w * gv[3].y;
+        const size_t e = (size_t)(4 * I + r) * W + c;
+        g[e] = gv[r];
+        d[e] = zr;
+        x[e] = make_float2(0.f, 0.f);
+        f0 = fmaf(gv[r].x, zr.x, f0);
+        f1 = fmaf(gv[r].y, zr.y, f1);
+        f2 = fmaf(gv[r].x, gv[r].x, f2);
+        f3 = fmaf(gv[r].y, gv[r].y, f3);
+      }
+    }
+    double v[4] = {f0, f1, f2, f3};
+    block_reduce<4>(v, W, sm.rs);
+    cg_start_scalars(sm, W);
+  }
+  cg32_loop(a, sm, x, g, d, q, itol);
+  {  // e = U - S x1 (float-float); w = x1; level 2 start: g = e, d = M^-1 e, x = 0
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    // x1 is read by neighbouring block rows: write w first, then overwrite x after a barrier.
+    for (int it = threadIdx.x; it < nb * W; it += TPB) {
+      if (!sm.act[c]) continue;
+      const int I = it / W;
+      gbff::acc are[4], aim[4];
+      bsr_row_ffx(a.m, a.m.sb_hi, a.m.sb_lo, x, W, c, I, are, aim);
+      float2 ev[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const size_t e = (size_t)(4 * I + r) * W + c;
+        const float4 u = U[e];
+        const gbff::ff er = gbff::ff_sub(gbff::ff{u.x, u.y}, gbff::acc_get(are[r]));
+        const gbff::ff ei = gbff::ff_sub(gbff::ff{u.z, u.w}, gbff::acc_get(aim[r]));
+        ev[r] = make_float2(er.hi + er.lo, ei.hi + ei.lo);
+        g[e] = ev[r];
+      }
+      const float4* Mi = reinterpret_cast<const float4*>(a.m.minv32 + (size_t)I * 16);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 mr = __ldg(Mi + r);
+        float2 zr;
+        zr.x = mr.x * ev[0].x + mr.y * ev[1].x + mr.z * ev[2].x + mr.w * ev[3].x;
+        zr.y = mr.x * ev[0].y + mr.y * ev[1].y + mr.z * ev[2].y + mr.w * ev[3].y;
+        d[(size_t)(4 * I + r) * W + c] = zr;
+        f0 = fmaf(ev[r].x, zr.x, f0);
+        f1 = fmaf(ev[r].y, zr.y, f1);
+        f2 = fmaf(ev[r].x, ev[r].x, f2);
+        f3 = fmaf(ev[r].y, ev[r].y, f3);
+      }
+    }
+    double v[4] = {f0, f1, f2, f3};
+    block_reduce<4>(v, W, sm.rs);  // contains the barrier that ends all reads of x1
+    for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+      if (!sm.act[c]) continue;
+      const float2 xv = x[e];
+      w[e] = make_float4(xv.x, 0.f, xv.y, 0.f);
+      x[e] = make_float2(0.f, 0.f);
+    }
+    cg_start_scalars(sm, W);  // its barrier orders the x / w writes too
+  }
+  cg32_loop(a, sm, x, g, d, q, itol);
+  for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+    if (!sm.act[c]) continue;
+    const float4 wv = w[e];
+    const float2 xv = x[e];
+    const gbff::ff re = gbff::ff_add(gbff::ff{wv.x, wv.y}, gbff::ff{xv.x, 0.f});
+    const gbff::ff im = gbff::ff_add(gbff::ff{wv.z, wv.w}, gbff::ff{xv.y, 0.f});
+    w[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+  __syncthreads();
+}
+
+}  // namespace gbk

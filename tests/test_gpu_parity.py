@@ -1,0 +1,165 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written here, derived in the design doc): plain FP64 path <= 1e-10
+relative to the largest reference magnitude of each output array; the
+reduced-precision path <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import chain_4orb, fermi_weights, ppv_chain, shift_grid
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+gbg = pytest.importorskip("paper_1603_09616_gb300")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch.cuda.set_device(0)
+    return torch.device("cuda", 0)
+
+
+# ------------------------------------------------------------------ SpMM
+@pytest.mark.parametrize("system_fn", [lambda: chain_4orb(37, seed=2), lambda: ppv_chain(5, seed=4)])
+@pytest.mark.parametrize("w", [1, 3, 16, 64])
+def test_spmm_fp64_and_fp32(dev, system_fn, w):
+    system = system_fn()
+    mat = gbg.Matrix(system)
+    H, S = system.dense()
+    rng = np.random.default_rng(w)
+    x = rng.standard_normal((system.n, w)) + 1j * rng.standard_normal((system.n, w))
+    xt = torch.from_numpy(x).to(dev)
+    for which, A in ((0, H), (1, S)):
+        y = to_np(mat.spmm(which, xt, prec="fp64"))
+        assert rel(y, A @ x) < 1e-14
+        y32 = to_np(mat.spmm(which, xt, prec="fp32"))
+        assert rel(y32, A @ x) < 2e-6
+    mat.close()
+
+
+# ------------------------------------------------------------------ shifted solve
+def run_case(dev, system, z, cols, prec, tol, maxit, panel=0, want_g=True, seed_shift=-1):
+    w_rho, w_edm = fermi_weights(z)
+    mat = gbg.Matrix(system)
+    out = gbg.shifted_solve(mat, z, cols, tol=tol, maxit=maxit, prec=prec, w_rho=w_rho, w_edm=w_edm,
+                            panel=panel, want_g=want_g, seed_shift=seed_shift)
+    torch.cuda.synchronize()
+    ref = oracle.solve_outputs(system, z, cols, w_rho, w_edm)
+    mat.close()
+    return out, ref
+
+
+def check_outputs(out, ref, bound, want_g=True):
+    assert out["status"] == 0, out["message"]
+    errs = {}
+    if want_g:
+        errs["g"] = rel(to_np(out["g_proj"]), ref["g_proj"])
+    for key in ("ldos", "rho", "edm", "q", "e_loc"):
+        errs[key] = rel(to_np(out[key]), ref[key])
+    for key, e in errs.items():
+        assert e < bound, (key, e, errs)
+    assert to_np(out["converged"]).all()
+    assert (to_np(out["resid"]) <= 1.0).all()
+    return errs
+
+
+@pytest.mark.parametrize("panel", [1, 4, 32])
+def test_fp64_chain_small_all_columns(dev, panel):
+    system = chain_4orb(16, seed=3)  # N = 64
+    z = shift_grid(-5, 5, 24, 0.1)
+    cols = np.arange(system.n, dtype=np.int32)
+    out, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 3000, panel=panel)
+    check_outputs(out, ref, 1e-10)
+
+
+def test_fp64_ragged_ppv_subset(dev):
+    system = ppv_chain(3, seed=7)  # N = 114: not a multiple of 4, hydrogen blocks
+    z = shift_grid(-10, 6, 40, 0.05)
+    cols = np.array([0, 1, 5, 31, 32, 33, 37, 60, 100, 113], np.int32)  # 10 columns: ragged last panel
+    out, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 5000, panel=4)
+    check_outputs(out, ref, 1e-10)
+
+
+def test_fp64_single_shift_single_column(dev):
+    system = chain_4orb(9, seed=1)
+    z = np.array([0.3 + 0.5j])
+    cols = np.array([system.n - 1], np.int32)
+    out, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 1000)
+    check_outputs(out, ref, 1e-10)
+
+
+def test_fp64_seed_choice_does_not_change_results(dev):
+    system = chain_4orb(12, seed=6)
+    z = shift_grid(-4, 4, 33, 0.08)
+    cols = np.arange(0, system.n, 5, dtype=np.int32)
+    a, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 3000, seed_shift=0)
+    b, _ = run_case(dev, system, z, cols, "fp64", 1e-12, 3000, seed_shift=32)
+    check_outputs(a, ref, 1e-10)
+    check_outputs(b, ref, 1e-10)
+
+
+def test_mixed_small(dev):
+    system = ppv_chain(3, seed=8)
+    z = shift_grid(-10, 6, 48, 0.05)
+    cols = np.arange(0, system.n, 7, dtype=np.int32)
+    out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=8)
+    check_outputs(out, ref, 1e-6)
+
+
+def test_maxit_exhaustion_reports_noconv(dev):
+    system = chain_4orb(30, seed=2)
+    z = shift_grid(-3, 3, 16, 0.01)
+    cols = np.array([0, 17, 50], np.int32)
+    w_rho, w_edm = fermi_weights(z)
+    mat = gbg.Matrix(system)
+    out = gbg.shifted_solve(mat, z, cols, tol=1e-12, maxit=5, prec="fp64", w_rho=w_rho, w_edm=w_edm)
+    assert out["status"] == gbg._binding.GB_ENOCONV
+    conv = to_np(out["converged"])
+    res = to_np(out["resid"])
+    assert not conv.all()
+    assert np.all((res <= 1e-12) == (conv == 1))
+    assert (to_np(out["iters"]) == 5).all()
+    mat.close()
+
+
+def test_invalid_parameters_rejected(dev):
+    system = chain_4orb(6, seed=2)
+    mat = gbg.Matrix(system)
+    z = np.array([0.1 + 0.1j])
+    with pytest.raises(gbg.GBError, match="EINVAL"):
+        gbg.shifted_solve(mat, np.array([0.1 - 0.1j]), [0], tol=1e-8, maxit=10)
+    with pytest.raises(gbg.GBError, match="EINVAL"):
+        gbg.shifted_solve(mat, z, [system.n], tol=1e-8, maxit=10)
+    with pytest.raises(gbg.GBError, match="EINVAL"):
+        gbg.shifted_solve(mat, z, [0], tol=1e-8, maxit=0)
+    with pytest.raises(gbg.GBError, match="EINVAL"):
+        gbg.shifted_solve(mat, z, [0], tol=1e-8, maxit=10, panel=3)
+    mat.close()
+
+
+def test_indefinite_overlap_reported(dev):
+    system = chain_4orb(10, seed=4)
+    s = system.s_val.copy()
+    rows = np.repeat(np.arange(system.n), np.diff(system.row_ptr))
+    off = rows != system.col_idx
+    s[off] *= 30.0  # diagonal blocks stay SPD, the whole S does not
+    system.s_val = s
+    assert np.linalg.eigvalsh(system.dense()[1]).min() < 0
+    mat = gbg.Matrix(system)
+    out = gbg.shifted_solve(mat, np.array([0.2 + 0.3j]), [0, 7], tol=1e-10, maxit=50,
+                            raise_on=())
+    assert out["status"] == gbg._binding.GB_ENOTSPD
+    mat.close()
