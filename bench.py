@@ -1,0 +1,365 @@
+"""Benchmark of the shifted Green's-function path on GB300.
+
+One step = one gb_shifted_solve over the whole workload: every (shift, RHS)
+pair of the 50-monomer PPV-like chain (N = 1900 orbitals, 128 shifts on
+[-15, 10] eV + 0.02i, all 1900 unit right-hand sides), mixed precision,
+tol 1e-8, reduced to LDOS / density / energy-density / charge / energy.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (dense
+LU per shift) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS·shift solves/s at rel err ≤1e-6 vs plain FP64 GPU; SpMM HBM GB/s % of peak"
+UNIT = "RHS·shift solves/s"
+FP32_LANES_PER_SM = 128
+NOMINAL_MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ppv1900")
+    ap.add_argument("--panel", type=int, default=0, help="RHS per panel (0: library choice)")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64-GPU accuracy check")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--maxit", type=int, default=0, help="override the workload's iteration cap")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one solve of the workload (for ncu captures) and exit")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                return json.load(f), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- op model
+def fp32_flops_model(info, W, iters, inner, prec):
+    """FP32 operations (add/mul = 1, fma = 2) the mixed path executes per panel.
+
+    Uses the padded 4x4 block entries B = 16 nnzb, N4 = 4 nb rows, the panel
+    width W, the outer iterations n and the inner FP32-CG iterations m of the
+    panel.  Costs per element (complex, W columns) follow the float-float
+    transformations in ffmath.cuh: a float-float multiply-accumulate is 15
+    flops (13 with a float operand), a complex float-float multiply 62, add 22.
+    """
+    B = 16 * info["nnzb"]
+    N4 = 4 * info["nb"]
+    per_outer = (B * 2 * W * 15 + 8 * 15 * N4 * W      # U = H p (float-float) + gamma dots
+                 + B * 2 * W * 13 + 22 * N4 * W        # e = U - S x1 (float-float)
+                 + 60 * N4 * W + 22 * N4 * W           # CG starts, w = x1 + x2
+                 + 426 * N4 * W + 168 * N4 * W)        # seed updates and dots
+    per_inner = B * 2 * W * 2 + 40 * N4 * W
+    return per_outer * iters + per_inner * inner
+
+
+def spmm_useful_flops(info, W, iters, inner):
+    return 4.0 * info["nnz"] * W * (2 * iters + inner)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    import paper_1603_09616_gb300 as gbg
+    from synth import workload
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    wl = workload(args.workload)
+    system, z, cols = wl["system"], wl["z"], wl["cols"]
+    K, nrhs = len(z), len(cols)
+    mat = gbg.Matrix(system)
+    info = mat.info
+    kw = dict(tol=wl["tol"], maxit=args.maxit or wl["maxit"], prec=wl["prec"], w_rho=wl["w_rho"],
+              w_edm=wl["w_edm"], panel=args.panel)
+    plan = gbg.solve_plan(mat, z, cols, tol=wl["tol"], maxit=wl["maxit"], prec=wl["prec"], panel=args.panel)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ws=None):
+        return gbg.shifted_solve(mat, z, cols, workspace=ws, **kw)
+
+    out = step()
+    ws = out["workspace"]
+    for _ in range(max(args.warmup - 1, 0)):
+        out = step(ws)
+    assert out["status"] == 0, out["message"]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step(ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    solves = K * nrhs
+    value = world * solves * args.steps / (total_ms / 1e3)
+    iters = out["iters"].cpu().numpy().astype(np.int64)
+    inner = out["inner_iters"].cpu().numpy().astype(np.int64)
+    W = plan["panel"]
+    npan = (nrhs + W - 1) // W
+    it_p = np.array([iters[p * W : (p + 1) * W].max() for p in range(npan)])
+    in_p = np.array([inner[p * W] for p in range(npan)])
+    flops = sum(fp32_flops_model(info, min(W, nrhs - p * W), float(it_p[p]), float(in_p[p]), wl["prec"])
+                for p in range(npan))
+    sm_mhz = clk["sm_mhz"] if clk else NOMINAL_MAX_SM_MHZ
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tf = 2.0 * FP32_LANES_PER_SM * nsm * NOMINAL_MAX_SM_MHZ * 1e6 / 1e12
+    achieved_tf = flops / (ms_per_step / 1e3) / 1e12
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32x2+f32 (f64 scalars)" if wl["prec"] == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "ppv1900: 50-monomer PPV-like chain, N=1900 orbitals (38/monomer), 128 shifts on "
+                        "[-15,10] eV + 0.02i, all 1900 RHS e_j, mixed precision, tol 1e-8",
+            "rhs": nrhs, "shifts": K, "n": int(system.n), "panel": W, "teams": plan["teams"],
+            "inner_cg_in_smem": plan["cg_smem"],
+            "l2": "256 MB flush between timed steps (workspace also exceeds L2)",
+            "parallelism": "replicas" if world > 1 else "1 GPU",
+        },
+        "krylov_iters_per_s": float(iters.sum()) * world * args.steps / (total_ms / 1e3),
+        "outer_iters": {"min": int(iters.min()), "median": int(np.median(iters)), "max": int(iters.max())},
+        "inner_per_outer": float(inner[::W].sum() / max(it_p.sum(), 1)),
+        "gpu_launches": args.steps,
+        "roofline": {
+            "kernel": "team_kernel<mixed>",
+            "bound": "alu",
+            "achieved": achieved_tf,
+            "peak": peak_tf,
+            "unit": "TFLOP/s",
+            "frac": achieved_tf / peak_tf,
+            "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max); FP32 op model "
+                           "of the float-float path",
+            "useful_spmm_tflops": spmm_useful_flops(info, 1, float(iters.sum()), float(inner[::W].sum()) * W)
+            / (ms_per_step / 1e3) / 1e12,
+        },
+        "clocks": clk,
+    }
+    # accuracy against the plain FP64 GPU path on sampled columns (outside the timed region)
+    if not args.no_check and rank == 0:
+        rng = np.random.default_rng(0)
+        sidx = np.sort(rng.choice(nrhs, size=16, replace=False))
+        ref = gbg.shifted_solve(mat, z, cols[sidx], tol=wl["tol"], maxit=wl["maxit"], prec="fp64",
+                                w_rho=wl["w_rho"], w_edm=wl["w_edm"], panel=1)
+        off = out["off"]
+        errs = {}
+        for key in ("ldos", "q", "e_loc"):
+            a = out[key].cpu().numpy()
+            a = a[:, sidx] if a.ndim == 2 else a[sidx]
+            b = ref[key].cpu().numpy()
+            errs[key] = float(np.abs(a - b).max() / np.abs(b).max())
+        for key in ("rho", "edm"):
+            a = out[key].cpu().numpy()
+            a = np.concatenate([a[off[j] : off[j + 1]] for j in sidx])
+            b = ref[key].cpu().numpy()
+            errs[key] = float(np.abs(a - b).max() / np.abs(b).max())
+        res["rel_err_vs_fp64_gpu"] = errs
+        res["rel_err_max"] = max(errs.values())
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = gbg.Matrix(system)  # host CSR -> device inside gb_build_bsr
+        o2 = gbg.shifted_solve(m2, z, cols, workspace=ws, **kw)
+        host = {k: o2[k].cpu() for k in ("ldos", "rho", "edm", "q", "e_loc", "iters", "converged", "resid")}
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        m2.close()
+        h2d = (system.row_ptr.nbytes + system.col_idx.nbytes + system.h_val.nbytes + system.s_val.nbytes
+               + K * 16 * 3 + nrhs * 4)
+        d2h = sum(v.numel() * v.element_size() for v in host.values())
+        res["e2e"] = {"value": world * solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+    # CPU oracle on a bounded sample (rank 0 at N = 1 only)
+    if not args.no_cpu and rank == 0 and world == 1:
+        res["cpu_baseline"] = cpu_oracle_rate(wl, n_shift=8)
+    mat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def cpu_oracle_rate(wl, n_shift: int):
+    import oracle
+
+    system, z = wl["system"], wl["z"]
+    idx = np.linspace(0, len(z) - 1, n_shift).round().astype(int)
+    zs = z[idx]
+    cols = wl["cols"]
+    t0 = time.perf_counter()
+    oracle.solve_outputs(system, zs, cols, wl["w_rho"][idx], wl["w_edm"][idx])
+    dt = time.perf_counter() - t0
+    return {"value": len(zs) * len(cols) / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(zs)} of {len(z)} shifts x all {len(cols)} RHS (dense complex LU per shift, "
+                      f"NumPy/SciPy FP64), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import workload
+
+    wl = workload(args.workload)
+    n_shift = 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, n_shift)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rates.append(cpu_oracle_rate(wl, n_shift))
+    total = time.perf_counter() - t0
+    solves = n_shift * len(wl["cols"]) * args.steps
+    value = solves / total
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "ppv1900 (bounded sample: 2 shifts x all 1900 RHS per step)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": rates[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def run_profile_case(args):
+    """One gb_shifted_solve of the workload (short with --maxit), for ncu."""
+    import torch
+
+    import paper_1603_09616_gb300 as gbg
+    from synth import workload
+
+    torch.cuda.set_device(0)
+    wl = workload(args.workload)
+    mat = gbg.Matrix(wl["system"])
+    out = gbg.shifted_solve(mat, wl["z"], wl["cols"], tol=wl["tol"], maxit=args.maxit or wl["maxit"],
+                            prec=wl["prec"], w_rho=wl["w_rho"], w_edm=wl["w_edm"], panel=args.panel,
+                            raise_on=(-1, -2, -3, -4))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.workload, "status": out["status"],
+                      "plan": gbg.solve_plan(mat, wl["z"], wl["cols"], prec=wl["prec"], panel=args.panel)}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.profile_case:
+        run_profile_case(a)
+    elif a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

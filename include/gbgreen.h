@@ -143,7 +143,8 @@ typedef struct {
   double inner_tol;      /* inner-CG relative residual; <= 0: library default
                             (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level) */
   int32_t panel;         /* RHS columns per panel (1..32); <= 0: auto            */
-  int32_t cluster;       /* CTAs per team (1, 2, 4, 8, 16); <= 0: auto           */
+  int32_t flags;         /* bit 1: keep the inner-CG vectors of a panel in shared
+                            memory when they fit (fewer teams per SM)           */
   int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
   int32_t reserved;
 } gb_solve_params;
@@ -161,6 +162,10 @@ typedef struct {
   uint8_t* converged; /* [K][nrhs] 1 if the pair met tol                        */
   double* resid;      /* [K][nrhs] recursive residual estimate at exit          */
   double* g_proj;     /* [K][P][2] optional: G_ij(z_k) (re, im) on the pattern  */
+  int32_t* inner_iters; /* [nrhs] inner-CG iterations of the column's panel,
+                           summed over the whole solve (all refinement levels) */
+  int32_t* col_status;  /* [nrhs] bit flags per column: 1 COCG breakdown, 2 S not
+                           SPD, 4 a shift missed tol, 8 inner CG hit its cap   */
 } gb_outputs;
 
 /*
@@ -168,6 +173,14 @@ typedef struct {
  * for (m, p).  Returns 0 if the parameters are invalid (see gb_last_error).
  */
 size_t gb_solve_workspace_size(const gb_matrix* m, const gb_solve_params* p);
+
+/*
+ * gb_solve_plan — the launch plan gb_shifted_solve would use for (m, p):
+ * plan[0] = RHS columns per panel, plan[1] = teams (CTAs) launched,
+ * plan[2] = 1 if the inner-CG vectors live in shared memory, plan[3] = their
+ * dynamic shared-memory bytes.  `plan` is a caller-owned host int32[4].
+ */
+gb_status gb_solve_plan(const gb_matrix* m, const gb_solve_params* p, int32_t* plan);
 
 /*
  * gb_shifted_solve — solve (z_k S - H) x = e_j for every shift and RHS, and

@@ -15,5 +15,6 @@ from ._binding import (  # noqa: F401
     load,
     pattern_offsets,
     shifted_solve,
+    solve_plan,
     workspace_bytes,
 )

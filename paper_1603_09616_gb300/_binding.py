@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgbgreen.so")
+LIB_PATH = os.environ.get("GBGREEN_LIB") or os.path.join(_HERE, "libgbgreen.so")
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD, GB_EBREAKDOWN, GB_ENOCONV, GB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 GB_FP64, GB_MIXED = 0, 1
@@ -30,6 +30,7 @@ EXPORTED = (
     "gb_free",
     "gb_spmm",
     "gb_solve_workspace_size",
+    "gb_solve_plan",
     "gb_shifted_solve",
 )
 
@@ -59,14 +60,15 @@ class SolveParams(C.Structure):
         ("prec", C.c_int32),
         ("inner_tol", C.c_double),
         ("panel", C.c_int32),
-        ("cluster", C.c_int32),
+        ("flags", C.c_int32),
         ("seed_shift", C.c_int32),
         ("reserved", C.c_int32),
     ]
 
 
 class Outputs(C.Structure):
-    _fields_ = [(f, C.c_void_p) for f in ("ldos", "rho", "edm", "q", "e_loc", "iters", "converged", "resid", "g_proj")]
+    _fields_ = [(f, C.c_void_p) for f in ("ldos", "rho", "edm", "q", "e_loc", "iters", "converged", "resid", "g_proj",
+                                            "inner_iters", "col_status")]
 
 
 _lib = None
@@ -97,6 +99,8 @@ def load() -> C.CDLL:
     lib.gb_spmm.argtypes = [C.c_void_p, C.c_int32, C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.gb_solve_workspace_size.restype = C.c_size_t
     lib.gb_solve_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
+    lib.gb_solve_plan.restype = C.c_int
+    lib.gb_solve_plan.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p]
     lib.gb_shifted_solve.restype = C.c_int
     lib.gb_shifted_solve.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p,
                                      C.c_size_t, C.c_void_p]
@@ -200,7 +204,7 @@ def pattern_offsets(system, cols) -> np.ndarray:
     return off
 
 
-def _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep):
+def _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep, flags=0):
     z = np.asarray(z, dtype=np.complex128)
     zr = np.ascontiguousarray(z.real)
     zi = np.ascontiguousarray(z.imag)
@@ -224,7 +228,7 @@ def _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shif
     p.prec = GB_FP64 if prec == "fp64" else GB_MIXED
     p.inner_tol = float(inner_tol)
     p.panel = int(panel)
-    p.cluster = 0
+    p.flags = int(flags)
     p.seed_shift = int(seed_shift)
     p.reserved = 0
     return p
@@ -239,8 +243,17 @@ def workspace_bytes(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", pa
     return int(nb)
 
 
+def solve_plan(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", panel=0, flags=0) -> dict:
+    """Launch plan of gb_shifted_solve: panel width, teams, shared-memory use."""
+    keep = []
+    p = _params(z, cols, tol, maxit, prec, None, None, 0.0, panel, -1, keep, flags)
+    plan = np.zeros(4, np.int32)
+    _check(load().gb_solve_plan(mat.handle, C.byref(p), _ptr(plan)))
+    return dict(panel=int(plan[0]), teams=int(plan[1]), cg_smem=bool(plan[2]), dyn_smem=int(plan[3]))
+
+
 def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
-                  inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, workspace=None, stream=None,
+                  inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, workspace=None, stream=None, flags=0,
                   raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD)):
     """Solve (z_k S - H) x = e_j for all shifts and columns; returns device tensors.
 
@@ -252,7 +265,7 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
 
     dev = torch.device("cuda", torch.cuda.current_device())
     keep = []
-    p = _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep)
+    p = _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep, flags)
     K, nrhs = p.nshift, p.nrhs
     lib = load()
     need = lib.gb_solve_workspace_size(mat.handle, C.byref(p))  # validates every parameter
@@ -271,6 +284,8 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
         converged=torch.empty((K, nrhs), dtype=torch.uint8, device=dev),
         resid=torch.empty((K, nrhs), **f64),
         g_proj=torch.empty((K, P), dtype=torch.complex128, device=dev) if want_g else None,
+        inner_iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        col_status=torch.empty(nrhs, dtype=torch.int32, device=dev),
     )
     o = Outputs()
     for f, _ in Outputs._fields_:

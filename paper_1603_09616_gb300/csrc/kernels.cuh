@@ -14,8 +14,18 @@
 
 namespace gbk {
 
-constexpr int TPB = 512;
+// Threads per team (CTA).  Several teams share an SM, so that one team's
+// barrier and memory stalls are covered by another team's work.
+#ifndef GB_TPB
+#define GB_TPB 512
+#endif
+#ifndef GB_UNROLL
+#define GB_UNROLL 2
+#endif
+constexpr int TPB = GB_TPB;
+constexpr int kUnroll = GB_UNROLL;  // blocks of a block row in flight per thread
 constexpr int NWARP = TPB / 32;
+constexpr int MIN_TEAMS_PER_SM = (512 / TPB) > 0 ? (512 / TPB) : 1;  // 128 registers per thread
 constexpr int WMAX = 32;
 constexpr int NVMAX = 4;
 
@@ -89,6 +99,7 @@ __device__ __forceinline__ void bsr_row_d(const DevMat& m, const double* __restr
 #pragma unroll
   for (int r = 0; r < 4; ++r) acc[r] = make_double2(0.0, 0.0);
   const int b1 = m.blk_ptr[I + 1];
+#pragma unroll kUnroll
   for (int b = m.blk_ptr[I]; b < b1; ++b) {
     const int J = m.blk_col[b];
     const double2* xr = x + (size_t)(4 * J) * W + c;
@@ -118,6 +129,7 @@ __device__ __forceinline__ void bsr_row_f(const DevMat& m, const float* __restri
 #pragma unroll
   for (int r = 0; r < 4; ++r) acc[r] = make_float2(0.f, 0.f);
   const int b1 = m.blk_ptr[I + 1];
+#pragma unroll kUnroll
   for (int b = m.blk_ptr[I]; b < b1; ++b) {
     const int J = m.blk_col[b];
     const float2* xr = x + (size_t)(4 * J) * W + c;
@@ -151,6 +163,7 @@ __device__ __forceinline__ void bsr_row_ff(const DevMat& m, const float* __restr
     gbff::acc_init(aim[r]);
   }
   const int b1 = m.blk_ptr[I + 1];
+#pragma unroll kUnroll
   for (int b = m.blk_ptr[I]; b < b1; ++b) {
     const int J = m.blk_col[b];
     const float4* xr = x + (size_t)(4 * J) * W + c;
@@ -184,6 +197,7 @@ __device__ __forceinline__ void bsr_row_ffx(const DevMat& m, const float* __rest
     gbff::acc_init(aim[r]);
   }
   const int b1 = m.blk_ptr[I + 1];
+#pragma unroll kUnroll
   for (int b = m.blk_ptr[I]; b < b1; ++b) {
     const int J = m.blk_col[b];
     const float2* xr = x + (size_t)(4 * J) * W + c;

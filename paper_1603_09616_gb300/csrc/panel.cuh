@@ -52,7 +52,7 @@ struct PanelSmemExtra {
 };
 
 template <bool MIX>
-__device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* ws) {
+__device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* ws, char* dyn) {
   using V = SeedT<MIX>;
   const int W = a.W, K = a.K, nb = a.m.nb, tid = threadIdx.x, c = tid % W;
   const size_t NE = (size_t)4 * nb * W;
@@ -76,6 +76,12 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
   double2* cgs = a.want_g ? wsp<double2>(ws, a.o_cg) : nullptr;
   const double2 sigma = a.sigma;
   const int WK = W * K;
+  // inner-CG vectors: shared memory when the panel fits (g, d, q), else global
+  using CgT = typename std::conditional<MIX, float2, double2>::type;
+  CgT* cg_x = wsp<CgT>(ws, a.o_x);
+  CgT* cg_g = a.cg_smem ? reinterpret_cast<CgT*>(dyn) : wsp<CgT>(ws, a.o_g);
+  CgT* cg_d = a.cg_smem ? cg_g + NE : wsp<CgT>(ws, a.o_d);
+  CgT* cg_q = a.cg_smem ? cg_d + NE : wsp<CgT>(ws, a.o_q);
 
   // ---------------------------------------------------------------- set-up
   if (tid < WMAX) {
@@ -102,6 +108,7 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
       wp += sm.act[i];
     }
     sm.Wp = wp;
+    sm.inner_count = 0;
   }
   for (int e = tid; e < WK; e += TPB) {
     const int cc = e / K;
@@ -121,10 +128,9 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 
   // r_0 = S^{-1} b
   if constexpr (MIX) {
-    inner_mixed(a, sm, rt, r, wsp<float2>(ws, a.o_x), wsp<float2>(ws, a.o_g), wsp<float2>(ws, a.o_d),
-                wsp<float2>(ws, a.o_q));
+    inner_mixed(a, sm, rt, r, cg_x, cg_g, cg_d, cg_q);
   } else {
-    cg64(a, sm, rt, r, wsp<double2>(ws, a.o_g), wsp<double2>(ws, a.o_d), wsp<double2>(ws, a.o_q));
+    cg64(a, sm, rt, r, cg_g, cg_d, cg_q);
   }
   {  // p = r, Sp = rt, rho_0 = r^T rt
     double v[2] = {0, 0};
@@ -229,10 +235,9 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 
     // w = S^{-1} U
     if constexpr (MIX) {
-      inner_mixed(a, sm, U, w, wsp<float2>(ws, a.o_x), wsp<float2>(ws, a.o_g), wsp<float2>(ws, a.o_d),
-                  wsp<float2>(ws, a.o_q));
+      inner_mixed(a, sm, U, w, cg_x, cg_g, cg_d, cg_q);
     } else {
-      cg64(a, sm, U, w, wsp<double2>(ws, a.o_g), wsp<double2>(ws, a.o_d), wsp<double2>(ws, a.o_q));
+      cg64(a, sm, U, w, cg_g, cg_d, cg_q);
     }
 
     if (tid < W && sm.act[tid]) {
@@ -576,10 +581,12 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
       if (a.e_loc) a.e_loc[col] = es;
     }
     if (a.iters) a.iters[col] = sm.nc[tid];
+    if (a.inner_iters) a.inner_iters[col] = sm.inner_count;
     int st = sm.st[tid];
     for (int k = 0; k < K; ++k)
       if (!(resk[tid * K + k] <= a.tol)) st |= kStNoConv;
     a.status[col] = st;
+    if (a.col_status) a.col_status[col] = st;
   }
   if (cgs && a.g_proj) {
     __syncthreads();
@@ -600,15 +607,16 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 }
 
 template <bool MIX>
-__global__ void __launch_bounds__(TPB, 1) team_kernel(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(TPB, MIN_TEAMS_PER_SM) team_kernel(const __grid_constant__ Args a) {
   __shared__ Smem sm;
   __shared__ PanelSmemExtra sx;
+  extern __shared__ __align__(16) char dyn_smem[];
   char* ws = a.team_ws + (size_t)blockIdx.x * a.team_bytes;
   for (;;) {
     if (threadIdx.x == 0) sm.panel = atomicAdd(a.panel_counter, 1);
     __syncthreads();
     if (sm.panel >= a.npanels) return;
-    solve_panel<MIX>(a, sm, sx, ws);
+    solve_panel<MIX>(a, sm, sx, ws, dyn_smem);
     __syncthreads();
   }
 }

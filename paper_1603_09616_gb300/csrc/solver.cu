@@ -265,7 +265,8 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
 namespace {
 
 struct Plan {
-  int W, KG, npanels, teams, Mcap, inner_maxit;
+  int W, KG, npanels, teams, teams_per_sm, Mcap, inner_maxit, cg_smem;
+  size_t dyn_smem;
   double itol;
   size_t team_bytes, header_bytes, total;
   size_t o_z, o_wr, o_we, o_cols, o_off, o_status, o_counter;
@@ -298,11 +299,29 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
   const int nsm = prop.multiProcessorCount;
 
+  // Panel width W and inner-CG placement.  The inner-CG vectors g, d, q of a
+  // panel (3 x N4 x W elements) may live in shared memory (flag bit 1) when
+  // they fit; by default they stay in global memory so that several teams
+  // share each SM.  Auto W: the widest panel that still gives every resident
+  // team a panel.
+  const size_t n4 = 4 * (size_t)m->nb;
+  const size_t cg_esz = p->prec == GB_FP64 ? 16 : 8;
+  const size_t smem_budget = (size_t)prop.sharedMemPerBlockOptin - 40 * 1024;
+  const bool want_smem = (p->flags & 2) != 0;
+  auto fits = [&](int w) { return want_smem && 3 * n4 * (size_t)w * cg_esz <= smem_budget; };
+  auto occupancy = [&](size_t dyn) {
+    int per_sm = 1;
+    const void* fn = p->prec == GB_FP64 ? (const void*)gbk::team_kernel<false> : (const void*)gbk::team_kernel<true>;
+    if (dyn > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gbk::TPB, dyn);
+    return (oe != cudaSuccess || per_sm < 1) ? 1 : per_sm;
+  };
   int W = p->panel;
   if (W <= 0) {
     W = 1;
     for (int cand : {32, 16, 8, 4, 2}) {
-      if ((p->nrhs + cand - 1) / cand >= nsm) {
+      const size_t dyn = fits(cand) ? 3 * n4 * (size_t)cand * cg_esz : 0;
+      if ((p->nrhs + cand - 1) / cand >= nsm * occupancy(dyn)) {
         W = cand;
         break;
       }
@@ -311,9 +330,12 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32)
     return fail(GB_EINVAL, "panel must be 1, 2, 4, 8, 16 or 32");
   pl->W = W;
+  pl->cg_smem = fits(W) ? 1 : 0;
+  pl->dyn_smem = pl->cg_smem ? 3 * n4 * (size_t)W * cg_esz : 0;
+  pl->teams_per_sm = occupancy(pl->dyn_smem);
   pl->KG = (p->nshift + 31) / 32;
   pl->npanels = (p->nrhs + W - 1) / W;
-  pl->teams = std::min(pl->npanels, nsm);
+  pl->teams = std::min(pl->npanels, nsm * pl->teams_per_sm);
   pl->Mcap = W * m->max_row;
   pl->inner_maxit = 500;
   // Inner-solve accuracy: the seed recurrence treats w = S^{-1} H p as exact,
@@ -375,6 +397,19 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
 }  // namespace
 
 extern "C" {
+
+gb_status gb_solve_plan(const gb_matrix* m, const gb_solve_params* p, int32_t* plan) {
+  clear_error();
+  if (!plan) return fail(GB_EINVAL, "plan is NULL");
+  Plan pl;
+  gb_status st = make_plan(m, p, false, &pl);
+  if (st != GB_OK) return st;
+  plan[0] = pl.W;
+  plan[1] = pl.teams;
+  plan[2] = pl.cg_smem;
+  plan[3] = (int32_t)pl.dyn_smem;
+  return GB_OK;
+}
 
 size_t gb_solve_workspace_size(const gb_matrix* m, const gb_solve_params* p) {
   clear_error();
@@ -454,15 +489,23 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
   a.q = out->q;
   a.e_loc = out->e_loc;
   a.iters = out->iters;
+  a.inner_iters = out->inner_iters;
+  a.col_status = out->col_status;
   a.conv = out->converged;
   a.resid = out->resid;
   a.g_proj = reinterpret_cast<double2*>(out->g_proj);
   a.P = ho[nrhs];
 
-  if (p->prec == GB_FP64)
-    gbk::team_kernel<false><<<pl.teams, gbk::TPB, 0, s>>>(a);
-  else
-    gbk::team_kernel<true><<<pl.teams, gbk::TPB, 0, s>>>(a);
+  a.cg_smem = pl.cg_smem;
+  if (p->prec == GB_FP64) {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<false><<<pl.teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  } else {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<true><<<pl.teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  }
   GB_CUDA(cudaGetLastError());
   std::vector<int> hst(nrhs);
   GB_CUDA(cudaMemcpyAsync(hst.data(), a.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));

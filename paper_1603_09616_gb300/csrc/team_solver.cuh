@@ -32,8 +32,11 @@
 namespace gbk {
 
 constexpr int CK = 64;                      // checkpoint interval of the pi recurrence
-constexpr double kRescaleBelow2 = 0x1p-64;  // rescale seed vectors when ||rt||^2 < 2^-64
-constexpr int kRescaleExp = 32;             // ... by 2^32 (exact)
+// The seed vectors are rescaled by an exact power of two whenever ||rt|| drops
+// below 2^-8, so that every vector of the mixed path (including the FP32
+// inner-solve right-hand sides, ~1e-7 of ||U||) stays far above FP32 underflow.
+constexpr double kRescaleBelow2 = 0x1p-16;  // rescale when ||rt||^2 < 2^-16
+constexpr int kRescaleExp = 8;              // ... by 2^8 (exact)
 
 struct Args {
   DevMat m;
@@ -52,12 +55,15 @@ struct Args {
   size_t o_r, o_rt, o_p, o_sp, o_u, o_w, o_g, o_d, o_q, o_x;
   size_t o_hr, o_ab, o_L, o_t, o_ck, o_pi, o_nk, o_res, o_buf, o_cp, o_cf, o_cg;
   int Mcap;
+  int cg_smem;  // 1: the inner-CG vectors g, d, q live in dynamic shared memory
   double* ldos;
   double* rho;
   double* edm;
   double* q;
   double* e_loc;
   int* iters;
+  int* inner_iters;
+  int* col_status;
   unsigned char* conv;
   double* resid;
   double2* g_proj;
@@ -71,7 +77,7 @@ constexpr int kStInner = 8;
 
 struct Smem {
   RedSmem rs;
-  int panel, Wp, flag;
+  int panel, Wp, flag, inner_count;
   int j[WMAX], mc[WMAX], off[WMAX + 1], act[WMAX], nc[WMAX], nact[WMAX], st[WMAX];
   double2 rho[WMAX], alpha[WMAX], beta[WMAX], aprev[WMAX], bprev[WMAX], gam[WMAX];
   double rt2[WMAX], scl[WMAX];
@@ -100,8 +106,8 @@ __device__ __noinline__ double2 pi_step(double2 cur, double2 prev, double2 a_n, 
 // Solves S x = f per real column (re, im parts separately), block-Jacobi
 // preconditioned, zero initial guess, until ||g|| <= itol ||f|| for every
 // active real column.
-__device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, double2* g, double2* d,
-                     double2* q) {
+__device__ void cg64(const Args& a, Smem& sm, const double2* __restrict__ f, double2* __restrict__ x,
+                     double2* __restrict__ g, double2* __restrict__ d, double2* __restrict__ q) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   {
     double v[4] = {0, 0, 0, 0};
@@ -141,19 +147,17 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, doub
   }
   const double it2 = a.itol * a.itol;
   for (int iter = 0;; ++iter) {
-    if (threadIdx.x == 0) {
-      int done = 1;
-      for (int k = 0; k < 2 * W; ++k)
-        if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = 0;
-      if (!done && iter >= a.inner_maxit) {
-        done = 1;
-        for (int k = 0; k < W; ++k)
-          if (sm.act[k]) sm.st[k] |= kStInner;
-      }
-      sm.flag = done;
+    // every thread evaluates the same test on the same shared scalars (the
+    // preceding barrier published them), so no extra barrier is needed
+    bool done = true;
+    for (int k = 0; k < 2 * W; ++k)
+      if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = false;
+    if (!done && iter >= a.inner_maxit) {
+      done = true;
+      if (threadIdx.x < W && sm.act[threadIdx.x]) sm.st[threadIdx.x] |= kStInner;
     }
-    __syncthreads();
-    if (sm.flag) break;
+    if (done) break;
+    if (threadIdx.x == 0) ++sm.inner_count;
     {  // q = S d, d^T q
       double v[2] = {0, 0};
       for (int it = threadIdx.x; it < nb * W; it += TPB) {
@@ -183,10 +187,10 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, doub
     }
     {  // x += a d, g -= a q, z = M^-1 g (into q), g^T z, g^T g
       double v[4] = {0, 0, 0, 0};
+      const double ar = sm.cg_a[2 * c], ai = sm.cg_a[2 * c + 1];
       for (int it = threadIdx.x; it < nb * W; it += TPB) {
         if (!sm.act[c]) continue;
         const int I = it / W;
-        const double ar = sm.cg_a[2 * c], ai = sm.cg_a[2 * c + 1];
         double2 gv[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -230,9 +234,9 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, doub
       __syncthreads();
     }
     // d = z + b d
+    const double br = sm.cg_b[2 * c], bi = sm.cg_b[2 * c + 1];
     for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
       if (!sm.act[c]) continue;
-      const double br = sm.cg_b[2 * c], bi = sm.cg_b[2 * c + 1];
       const double2 zv = q[e];
       double2 dv = d[e];
       dv.x = fma(br, dv.x, zv.x);
@@ -246,23 +250,22 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* f, double2* x, doub
 // ------------------------------------------------------------ inner CG, FP32 loop
 // Runs on (x, g, d) already initialised (x = 0, g = rhs, d = M^-1 g) with
 // cg_rho / cg_un / cg_gg set.  FP32 vectors, FP64 scalars.
-__device__ void cg32_loop(const Args& a, Smem& sm, float2* x, float2* g, float2* d, float2* q, double itol) {
+__device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ g,
+                          float2* __restrict__ d, float2* __restrict__ q, double itol) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   const double it2 = itol * itol;
   for (int iter = 0;; ++iter) {
-    if (threadIdx.x == 0) {
-      int done = 1;
-      for (int k = 0; k < 2 * W; ++k)
-        if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = 0;
-      if (!done && iter >= a.inner_maxit) {
-        done = 1;
-        for (int k = 0; k < W; ++k)
-          if (sm.act[k]) sm.st[k] |= kStInner;
-      }
-      sm.flag = done;
+    // every thread evaluates the same test on the same shared scalars (the
+    // preceding barrier published them), so no extra barrier is needed
+    bool done = true;
+    for (int k = 0; k < 2 * W; ++k)
+      if (sm.act[k >> 1] && sm.cg_gg[k] > it2 * sm.cg_un[k]) done = false;
+    if (!done && iter >= a.inner_maxit) {
+      done = true;
+      if (threadIdx.x < W && sm.act[threadIdx.x]) sm.st[threadIdx.x] |= kStInner;
     }
-    __syncthreads();
-    if (sm.flag) break;
+    if (done) break;
+    if (threadIdx.x == 0) ++sm.inner_count;
     {
       double v[2] = {0, 0};
       float v0 = 0.f, v1 = 0.f;
@@ -287,18 +290,24 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* x, float2* g, float2*
         const int cc = threadIdx.x >> 1, p = threadIdx.x & 1;
         const double dq = sm.rs.scal[p * WMAX + cc];
         double al = 0.0;
-        if (dq > 0.0) al = sm.cg_rho[threadIdx.x] / dq;
-        else if (dq < 0.0 && sm.act[cc]) sm.st[cc] |= kStNotSPD;
+        if (dq > 0.0) {
+          al = sm.cg_rho[threadIdx.x] / dq;
+        } else if (sm.act[cc] && sm.cg_gg[threadIdx.x] > 0.0) {
+          // no curvature left in FP32 (d^T S d <= 0 with a nonzero residual):
+          // this real column cannot progress; stop it and report it
+          sm.st[cc] |= (dq < 0.0 ? kStNotSPD : 0) | kStInner;
+          sm.cg_gg[threadIdx.x] = 0.0;
+        }
         sm.cg_a[threadIdx.x] = al;
       }
       __syncthreads();
     }
     {
       float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+      const float ar = (float)sm.cg_a[2 * c], ai = (float)sm.cg_a[2 * c + 1];
       for (int it = threadIdx.x; it < nb * W; it += TPB) {
         if (!sm.act[c]) continue;
         const int I = it / W;
-        const float ar = (float)sm.cg_a[2 * c], ai = (float)sm.cg_a[2 * c + 1];
         float2 gv[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -340,9 +349,9 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* x, float2* g, float2*
       }
       __syncthreads();
     }
+    const float br = (float)sm.cg_b[2 * c], bi = (float)sm.cg_b[2 * c + 1];
     for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
       if (!sm.act[c]) continue;
-      const float br = (float)sm.cg_b[2 * c], bi = (float)sm.cg_b[2 * c + 1];
       const float2 zv = q[e];
       float2 dv = d[e];
       dv.x = fmaf(br, dv.x, zv.x);
@@ -367,8 +376,9 @@ __device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
 // ------------------------------------------------------------ inner solve, mixed
 // w = S^{-1} U to ~FP64 accuracy: FP32 CG on hi(U), a float-float residual
 // e = U - S x1, FP32 CG on e, w = x1 + x2 (float-float).
-__device__ void inner_mixed(const Args& a, Smem& sm, const float4* U, float4* w, float2* x, float2* g,
-                            float2* d, float2* q) {
+__device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ U, float4* __restrict__ w,
+                            float2* __restrict__ x, float2* __restrict__ g, float2* __restrict__ d,
+                            float2* __restrict__ q) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   const double itol = a.itol;
   {  // level 1 start: g = hi(U), d = M^-1 g, x = 0

@@ -310,7 +310,7 @@ def workload(name: str) -> dict:
         sys_ = ppv_chain(50, seed=1)
         z = shift_grid(-15.0, 10.0, 128, 0.02)
         cols = np.arange(sys_.n, dtype=np.int32)
-        tol, maxit, prec = 1e-8, 3000, "mixed"
+        tol, maxit, prec = 1e-8, 16000, "mixed"
     elif name == "bundle169":
         sys_ = ppv_bundle(seed=3)
         z = shift_grid(-15.0, 10.0, 64, 0.02)

@@ -1,0 +1,106 @@
+"""Parity at the workload sizes.
+
+chain800 : 200 sites x 4 orbitals, 64 shifts on [-12, 12] + 0.05i, plain FP64.
+ppv1900  : 50-monomer PPV-like chain, 128 shifts on [-15, 10] + 0.02i, mixed.
+
+Sampled columns are compared with the dense-LU oracle element by element.
+The full 1900-column launch (the benchmark's configuration) is also checked
+at full size through identities that hold for the complete column set:
+  sum_j (G(z_k) S)_jj = sum_l 1/(z_k - lambda_l)      (trace identity)
+  sum_j q_j = sum_k Im(c_k sum_l 1/(z_k - lambda_l))  (total charge)
+with lambda_l the generalized eigenvalues of (H, S).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+gbg = pytest.importorskip("paper_1603_09616_gb300")
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def sample_cols(n, k, seed):
+    rng = np.random.default_rng(seed)
+    c = set(rng.choice(n, size=k - 2, replace=False).tolist()) | {0, n - 1}
+    return np.array(sorted(c), dtype=np.int32)
+
+
+@pytest.fixture(scope="module")
+def ppv():
+    torch.cuda.set_device(0)
+    wl = workload("ppv1900")
+    mat = gbg.Matrix(wl["system"])
+    cols = sample_cols(wl["system"].n, 12, seed=11)
+    ref = oracle.solve_outputs(wl["system"], wl["z"], cols, wl["w_rho"], wl["w_edm"])
+    yield wl, mat, cols, ref
+    mat.close()
+
+
+def test_chain800_fp64_sampled_columns():
+    torch.cuda.set_device(0)
+    wl = workload("chain800")
+    system, z = wl["system"], wl["z"]
+    cols = sample_cols(system.n, 24, seed=5)
+    mat = gbg.Matrix(system)
+    # maxit: the mid-band shifts need ~4.4k iterations at eta = 0.05 (800 is too few)
+    out = gbg.shifted_solve(mat, z, cols, tol=1e-11, maxit=8000, prec="fp64", w_rho=wl["w_rho"],
+                            w_edm=wl["w_edm"], want_g=True)
+    mat.close()
+    assert out["status"] == 0, out["message"]
+    ref = oracle.solve_outputs(system, z, cols, wl["w_rho"], wl["w_edm"])
+    assert rel(to_np(out["g_proj"]), ref["g_proj"]) < 1e-10
+    for key in ("ldos", "rho", "edm", "q", "e_loc"):
+        assert rel(to_np(out[key]), ref[key]) < 1e-10, key
+
+
+def test_ppv1900_mixed_sampled_vs_oracle_and_fp64(ppv):
+    wl, mat, cols, ref = ppv
+    mixed = gbg.shifted_solve(mat, wl["z"], cols, tol=wl["tol"], maxit=wl["maxit"], prec="mixed",
+                              w_rho=wl["w_rho"], w_edm=wl["w_edm"], want_g=True)
+    assert mixed["status"] == 0, mixed["message"]
+    for key in ("ldos", "rho", "edm", "q", "e_loc"):
+        assert rel(to_np(mixed[key]), ref[key]) < 1e-6, key
+    assert rel(to_np(mixed["g_proj"]), ref["g_proj"]) < 1e-6
+    fp64 = gbg.shifted_solve(mat, wl["z"], cols, tol=wl["tol"], maxit=wl["maxit"], prec="fp64",
+                             w_rho=wl["w_rho"], w_edm=wl["w_edm"])
+    assert fp64["status"] == 0, fp64["message"]
+    for key in ("ldos", "rho", "edm", "q", "e_loc"):
+        assert rel(to_np(mixed[key]), to_np(fp64[key])) < 1e-6, key
+
+
+def test_ppv1900_full_launch(ppv):
+    wl, mat, cols, ref = ppv
+    system, z = wl["system"], wl["z"]
+    all_cols = np.arange(system.n, dtype=np.int32)
+    out = gbg.shifted_solve(mat, z, all_cols, tol=wl["tol"], maxit=wl["maxit"], prec="mixed",
+                            w_rho=wl["w_rho"], w_edm=wl["w_edm"])
+    assert out["status"] == 0, out["message"]
+    assert to_np(out["converged"]).all()
+    # sampled columns of the full launch against the oracle
+    off = out["off"]
+    ldos = to_np(out["ldos"])
+    rho = to_np(out["rho"])
+    q = to_np(out["q"])
+    assert rel(ldos[:, cols], ref["ldos"]) < 1e-6
+    rho_s = np.concatenate([rho[off[j] : off[j + 1]] for j in cols])
+    assert rel(rho_s, ref["rho"]) < 1e-6
+    assert rel(q[cols], ref["q"]) < 1e-6
+    # full-size identities from the generalized eigenvalues
+    H, S = system.dense()
+    lam = sla.eigh(H, S, eigvals_only=True)
+    tr = np.array([np.sum(1.0 / (zk - lam)) for zk in z])
+    assert rel(ldos.sum(axis=1), -np.imag(tr) / np.pi) < 1e-6
+    charge = np.sum(np.imag(wl["w_rho"] * tr))
+    assert abs(q.sum() - charge) < 1e-6 * abs(charge)
