@@ -73,7 +73,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(os.environ.get("GB_CLOCK_LOG_DIR", "/tmp"), f"gbgreen_clocks_{gpu_index}.csv")
 
     def start(self):
         try:

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-Tolerances (written here, derived in the design doc): plain FP64 path <= 1e-10
+Tolerances: plain FP64 path <= 1e-10 (the bound for the FP64 solver)
 relative to the largest reference magnitude of each output array; the
 reduced-precision path <= 1e-6.
 """
