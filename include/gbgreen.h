@@ -196,6 +196,38 @@ gb_status gb_solve_plan(const gb_matrix* m, const gb_solve_params* p, int32_t* p
 gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
                            void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * gb_shifted_solve_static — gb_shifted_solve without any allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate once they run — an application whose device memory belongs to
+ * another runtime's pool that already claims the whole GPU, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  Same arguments and results as gb_shifted_solve (caller-owned
+ * outputs), but the scratch is a fixed per-device array inside the library of
+ * gb_static_scratch_bytes() bytes (32 MiB), which every GPU that loads the
+ * library holds until the process exits; the launch header and status are
+ * staged in fixed host buffers.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ *   - The first call on a device looks up the scratch's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture on the device.
+ *   - Problems whose scratch exceeds the array, or with nrhs > 4096, are
+ *     rejected (GB_ENOMEM / GB_EINVAL) with a message naming the limit; the
+ *     number of concurrent teams is reduced when that lets the problem fit
+ *     (results do not depend on it).
+ *   - Every call shares the one array and leaves its contents behind; the call
+ *     re-initialises everything it reads (the work counter is cleared from
+ *     the host).  Calls whose GPU work overlaps (other streams, other host
+ *     threads) race on the array: serialise them.
+ * Synchronous.
+ */
+gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
+                                  void* stream);
+
+/* Size in bytes of the per-device scratch of gb_shifted_solve_static. */
+size_t gb_static_scratch_bytes(void);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* gb_last_error(void);
 

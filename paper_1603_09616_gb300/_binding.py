@@ -32,6 +32,8 @@ EXPORTED = (
     "gb_solve_workspace_size",
     "gb_solve_plan",
     "gb_shifted_solve",
+    "gb_shifted_solve_static",
+    "gb_static_scratch_bytes",
 )
 
 
@@ -104,6 +106,9 @@ def load() -> C.CDLL:
     lib.gb_shifted_solve.restype = C.c_int
     lib.gb_shifted_solve.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p,
                                      C.c_size_t, C.c_void_p]
+    lib.gb_shifted_solve_static.restype = C.c_int
+    lib.gb_shifted_solve_static.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p]
+    lib.gb_static_scratch_bytes.restype = C.c_size_t
     _lib = lib
     return lib
 
@@ -301,4 +306,44 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
     res["message"] = lib.gb_last_error().decode()
     res["off"] = off
     res["workspace"] = workspace
+    return res
+
+
+def shifted_solve_static(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
+                         inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, stream=None, flags=0):
+    """Like :func:`shifted_solve`, through gb_shifted_solve_static (no scratch
+    allocation: the library's fixed per-device scratch is used)."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    p = _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep, flags)
+    K, nrhs = p.nshift, p.nrhs
+    lib = load()
+    if lib.gb_solve_workspace_size(mat.handle, C.byref(p)) == 0:  # validates the parameters
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    off = pattern_offsets(mat.system, cols)
+    P = int(off[-1])
+    f64 = dict(dtype=torch.float64, device=dev)
+    res = dict(
+        ldos=torch.empty((K, nrhs), **f64),
+        rho=torch.empty(P, **f64) if w_rho is not None else None,
+        edm=torch.empty(P, **f64) if w_edm is not None else None,
+        q=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        e_loc=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        converged=torch.empty((K, nrhs), dtype=torch.uint8, device=dev),
+        resid=torch.empty((K, nrhs), **f64),
+        g_proj=torch.empty((K, P), dtype=torch.complex128, device=dev) if want_g else None,
+        inner_iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        col_status=torch.empty(nrhs, dtype=torch.int32, device=dev),
+    )
+    o = Outputs()
+    for f, _ in Outputs._fields_:
+        t = res[f]
+        setattr(o, f, C.c_void_p(t.data_ptr()) if t is not None else None)
+    st = lib.gb_shifted_solve_static(mat.handle, C.byref(p), C.byref(o), _stream_handle(stream))
+    res["status"] = st
+    res["message"] = lib.gb_last_error().decode()
+    res["off"] = off
     return res

@@ -521,3 +521,149 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ allocation-free solve
+// gb_shifted_solve_static: the same solve for callers that may not allocate
+// memory once they are running — e.g. an application whose device memory is
+// owned by another runtime's pool that claims the whole GPU, or a latency-
+// critical loop in which cudaMalloc's implicit device synchronisation is not
+// acceptable.  Its device scratch is one file-scope array below; its host-side
+// staging uses fixed static buffers.  Nothing here calls cudaMalloc, cudaFree
+// or any other allocating routine.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
+constexpr int kStaticMaxRhs = 4096;
+constexpr int kMaxDevices = 64;
+
+// Device scratch shared by every gb_shifted_solve_static call on a device.  In
+// host code this name is only a stand-in for the symbol: its device address is
+// obtained once per device with cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;                      // guards the table and the host staging buffers
+void* g_static_addr[kMaxDevices] = {nullptr};  // device address of g_static_scratch per device
+alignas(256) char g_static_hdr[256 * 1024];  // host staging of the launch header
+int g_static_status[kStaticMaxRhs];          // host copy of the per-column status
+
+}  // namespace
+
+extern "C" {
+
+gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
+                                  void* stream) {
+  clear_error();
+  if (!out) return fail(GB_EINVAL, "outputs is NULL");
+  if (!p) return fail(GB_EINVAL, "params is NULL");
+  if (p->nrhs > kStaticMaxRhs) return fail(GB_EINVAL, "nrhs %d exceeds the static limit %d", p->nrhs, kStaticMaxRhs);
+  Plan pl;
+  const bool want_g = out->g_proj != nullptr;
+  gb_status st = make_plan(m, p, want_g, &pl);
+  if (st != GB_OK) return st;
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device %d differs from the matrix's device %d", dev, m->device);
+  if (dev < 0 || dev >= kMaxDevices) return fail(GB_EINVAL, "device ordinal %d out of range", dev);
+  if (pl.header_bytes > sizeof(g_static_hdr)) return fail(GB_EINVAL, "too many shifts/columns for the static path");
+  // fewer teams than the allocating path if needed: results do not depend on it
+  const size_t hdr_al = align256(pl.header_bytes);
+  if (hdr_al + pl.team_bytes > kStaticScratchBytes)
+    return fail(GB_ENOMEM, "problem needs %zu bytes of scratch per team; the static scratch holds %zu bytes",
+                hdr_al + pl.team_bytes, kStaticScratchBytes);
+  const int teams = (int)std::min<size_t>(pl.teams, (kStaticScratchBytes - hdr_al) / pl.team_bytes);
+
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_addr[dev] == nullptr) {  // first call on this device: look up the scratch address
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[dev] = ptr;
+  }
+  char* wsb = static_cast<char*>(g_static_addr[dev]);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  const int K = p->nshift, nrhs = p->nrhs;
+  std::memset(g_static_hdr, 0, pl.header_bytes);  // includes the panel counter, which must start at 0
+  double2* hz = reinterpret_cast<double2*>(g_static_hdr + pl.o_z);
+  double2* hwr = reinterpret_cast<double2*>(g_static_hdr + pl.o_wr);
+  double2* hwe = reinterpret_cast<double2*>(g_static_hdr + pl.o_we);
+  for (int k = 0; k < K; ++k) {
+    hz[k] = make_double2(p->z_re[k], p->z_im[k]);
+    hwr[k] = p->w_rho ? make_double2(p->w_rho[2 * k], p->w_rho[2 * k + 1]) : make_double2(0, 0);
+    hwe[k] = p->w_edm ? make_double2(p->w_edm[2 * k], p->w_edm[2 * k + 1]) : make_double2(0, 0);
+  }
+  std::memcpy(g_static_hdr + pl.o_cols, p->rhs_cols, sizeof(int) * nrhs);
+  long long* ho = reinterpret_cast<long long*>(g_static_hdr + pl.o_off);
+  ho[0] = 0;
+  for (int i = 0; i < nrhs; ++i) {
+    const int j = p->rhs_cols[i];
+    ho[i + 1] = ho[i] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+  }
+  GB_CUDA(cudaMemcpyAsync(wsb, g_static_hdr, pl.header_bytes, cudaMemcpyHostToDevice, s));
+
+  gbk::Args& a = pl.a;
+  a.m = m->dm;
+  a.K = K;
+  a.W = pl.W;
+  a.KG = pl.KG;
+  a.nrhs = nrhs;
+  a.npanels = pl.npanels;
+  a.maxit = p->maxit;
+  a.inner_maxit = pl.inner_maxit;
+  a.has_rho = p->w_rho != nullptr;
+  a.has_edm = p->w_edm != nullptr;
+  a.want_g = want_g;
+  a.tol = p->tol;
+  a.itol = pl.itol;
+  const int seed = p->seed_shift >= 0 ? p->seed_shift : K / 2;
+  a.sigma = make_double2(p->z_re[seed], p->z_im[seed]);
+  a.z = reinterpret_cast<const double2*>(wsb + pl.o_z);
+  a.w_rho = reinterpret_cast<const double2*>(wsb + pl.o_wr);
+  a.w_edm = reinterpret_cast<const double2*>(wsb + pl.o_we);
+  a.rhs_cols = reinterpret_cast<const int*>(wsb + pl.o_cols);
+  a.out_off = reinterpret_cast<const long long*>(wsb + pl.o_off);
+  a.status = reinterpret_cast<int*>(wsb + pl.o_status);
+  a.panel_counter = reinterpret_cast<int*>(wsb + pl.o_counter);
+  a.team_ws = wsb + hdr_al;
+  a.team_bytes = pl.team_bytes;
+  a.Mcap = pl.Mcap;
+  a.ldos = out->ldos;
+  a.rho = out->rho;
+  a.edm = out->edm;
+  a.q = out->q;
+  a.e_loc = out->e_loc;
+  a.iters = out->iters;
+  a.inner_iters = out->inner_iters;
+  a.col_status = out->col_status;
+  a.conv = out->converged;
+  a.resid = out->resid;
+  a.g_proj = reinterpret_cast<double2*>(out->g_proj);
+  a.P = ho[nrhs];
+  a.cg_smem = pl.cg_smem;
+  if (p->prec == GB_FP64) {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<false><<<teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  } else {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<true><<<teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  }
+  GB_CUDA(cudaGetLastError());
+  GB_CUDA(cudaMemcpyAsync(g_static_status, a.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  int any = 0;
+  for (int i = 0; i < nrhs; ++i) any |= g_static_status[i];
+  if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
+  if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
+  if (any & (gbk::kStNoConv | gbk::kStInner))
+    return fail(GB_ENOCONV, "some (shift, column) pairs did not reach tol within maxit%s",
+                (any & gbk::kStInner) ? " (inner CG hit its cap)" : "");
+  return GB_OK;
+}
+
+size_t gb_static_scratch_bytes(void) { return kStaticScratchBytes; }
+
+}  // extern "C"
