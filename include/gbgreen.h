@@ -197,6 +197,36 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gb_shifted_solve_batched — many independent systems in one persistent launch.
+ *
+ * Each system s solves (z_k S_s - H_s) x = e_j for its own shifts and columns
+ * (params[s]) on its own matrix mats[s] and writes its own outputs outs[s];
+ * all systems share one precision and one device.  Work items are (system,
+ * panel of `panel` columns) pairs taken from a device counter, largest systems
+ * first; converged shifts and columns retire inside their panel.  panel <= 0:
+ * library choice.  `workspace`: gb_batched_workspace_size bytes, 256-byte
+ * aligned.  Synchronous; the status is the worst over all systems.
+ */
+gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                   const gb_outputs* outs, int32_t panel, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for gb_shifted_solve_batched (want_g: any system asks for g_proj). */
+size_t gb_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                 int32_t panel, int32_t want_g);
+
+/*
+ * gb_tune_panel_batched — autotuner for the batched panel width: runs the
+ * batch with every maxit capped at probe_maxit for panel widths {4, 8, 16, 32},
+ * times each launch on `stream`, and returns the fastest in *best_panel
+ * (times_ms: optional host float[4], -1 for a width that did not fit the
+ * workspace).  The outputs are overwritten by the probe runs.
+ */
+gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                const gb_outputs* outs, int32_t probe_maxit, void* workspace,
+                                size_t workspace_bytes, void* stream, int32_t* best_panel, float* times_ms);
+
+/*
  * gb_shifted_solve_static — gb_shifted_solve without any allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that may

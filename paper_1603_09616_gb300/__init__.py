@@ -15,6 +15,7 @@ from ._binding import (  # noqa: F401
     load,
     pattern_offsets,
     shifted_solve,
+    shifted_solve_batched,
     shifted_solve_static,
     solve_plan,
     workspace_bytes,

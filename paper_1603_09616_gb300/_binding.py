@@ -34,6 +34,9 @@ EXPORTED = (
     "gb_shifted_solve",
     "gb_shifted_solve_static",
     "gb_static_scratch_bytes",
+    "gb_shifted_solve_batched",
+    "gb_batched_workspace_size",
+    "gb_tune_panel_batched",
 )
 
 
@@ -109,6 +112,14 @@ def load() -> C.CDLL:
     lib.gb_shifted_solve_static.restype = C.c_int
     lib.gb_shifted_solve_static.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p]
     lib.gb_static_scratch_bytes.restype = C.c_size_t
+    lib.gb_shifted_solve_batched.restype = C.c_int
+    lib.gb_shifted_solve_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                             C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.gb_batched_workspace_size.restype = C.c_size_t
+    lib.gb_batched_workspace_size.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]
+    lib.gb_tune_panel_batched.restype = C.c_int
+    lib.gb_tune_panel_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                          C.c_size_t, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]
     _lib = lib
     return lib
 
@@ -347,3 +358,87 @@ def shifted_solve_static(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64
     res["message"] = lib.gb_last_error().decode()
     res["off"] = off
     return res
+
+
+def _alloc_outputs(mat, K, cols, w_rho, w_edm, want_g, dev):
+    import torch
+
+    nrhs = len(cols)
+    off = pattern_offsets(mat.system, cols)
+    P = int(off[-1])
+    f64 = dict(dtype=torch.float64, device=dev)
+    res = dict(
+        ldos=torch.empty((K, nrhs), **f64),
+        rho=torch.empty(P, **f64) if w_rho is not None else None,
+        edm=torch.empty(P, **f64) if w_edm is not None else None,
+        q=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        e_loc=torch.empty(nrhs, **f64) if w_rho is not None else None,
+        iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        converged=torch.empty((K, nrhs), dtype=torch.uint8, device=dev),
+        resid=torch.empty((K, nrhs), **f64),
+        g_proj=torch.empty((K, P), dtype=torch.complex128, device=dev) if want_g else None,
+        inner_iters=torch.empty(nrhs, dtype=torch.int32, device=dev),
+        col_status=torch.empty(nrhs, dtype=torch.int32, device=dev),
+    )
+    o = Outputs()
+    for f, _ in Outputs._fields_:
+        t = res[f]
+        setattr(o, f, C.c_void_p(t.data_ptr()) if t is not None else None)
+    res["off"] = off
+    return res, o
+
+
+def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, workspace=None, stream=None,
+                          tune_probe_maxit=0):
+    """Solve many independent systems in one persistent launch.
+
+    ``problems`` is a list of dicts with keys z, cols, tol, maxit and optional
+    w_rho, w_edm (one per matrix in ``mats``).  With ``tune_probe_maxit > 0``
+    the panel width is first picked by the library's autotuner
+    (gb_tune_panel_batched) on probe runs of that many iterations.  Returns a
+    list of per-system result dicts plus the batch status/message/panel.
+    """
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib = load()
+    nsys = len(mats)
+    keep = []
+    params = (SolveParams * nsys)()
+    outs = (Outputs * nsys)()
+    results = []
+    for s_, (mat, pr) in enumerate(zip(mats, problems)):
+        p = _params(pr["z"], pr["cols"], pr["tol"], pr["maxit"], prec, pr.get("w_rho"), pr.get("w_edm"), 0.0,
+                    panel, -1, keep)
+        params[s_] = p
+        res, o = _alloc_outputs(mat, len(pr["z"]), pr["cols"], pr.get("w_rho"), pr.get("w_edm"), want_g, dev)
+        outs[s_] = o
+        results.append(res)
+    handles = (C.c_void_p * nsys)(*[m.handle.value for m in mats])
+    info = {}
+    if tune_probe_maxit > 0:
+        probe = (SolveParams * nsys)(*params)
+        for q in range(nsys):
+            probe[q].maxit = min(probe[q].maxit, tune_probe_maxit)
+        need = max(lib.gb_batched_workspace_size(nsys, handles, probe, w, int(want_g)) for w in (4, 8, 16, 32))
+        tws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+        best = C.c_int32()
+        times = np.zeros(4, np.float32)
+        _check(lib.gb_tune_panel_batched(nsys, handles, probe, outs, int(tune_probe_maxit),
+                                         C.c_void_p(tws.data_ptr()), C.c_size_t(tws.numel()),
+                                         _stream_handle(stream), C.byref(best), _ptr(times)))
+        panel = int(best.value)
+        info["tuned_panel"] = panel
+        info["tune_times_ms"] = times.tolist()
+        del tws
+    need = lib.gb_batched_workspace_size(nsys, handles, params, int(panel), int(want_g))
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    st = lib.gb_shifted_solve_batched(nsys, handles, params, outs, int(panel), C.c_void_p(workspace.data_ptr()),
+                                      C.c_size_t(workspace.numel()), _stream_handle(stream))
+    if st in (GB_EINVAL, GB_ENOMEM, GB_ECUDA):
+        _check(st)
+    info.update(status=st, message=lib.gb_last_error().decode(), panel=panel, workspace=workspace)
+    return results, info

@@ -181,12 +181,23 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
       gbff::acc_init(d1);
       gbff::acc_init(d2);
       gbff::acc_init(d3);
+#if GB_WARP_SPMM
+      const int lane = tid & 31;
+      const bool act = sm.act[c] != 0;
+      for (int I = tid >> 5; I < nb; I += NWARP) {
+#else
       for (int it = tid; it < nb * W; it += TPB) {
         if (!sm.act[c]) continue;
         const int I = it / W;
+#endif
         if constexpr (MIX) {
           gbff::acc are[4], aim[4];
+#if GB_WARP_SPMM
+          wbsr_row_ff(a.m, a.m.hb_hi, a.m.hb_lo, p, W, W, lane, I, act, are, aim);
+          if (lane >= W || !act) continue;
+#else
           bsr_row_ff(a.m, a.m.hb_hi, a.m.hb_lo, p, W, c, I, are, aim);
+#endif
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
             const size_t e = (size_t)(4 * I + rr) * W + c;
@@ -205,7 +216,12 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
           }
         } else {
           double2 acc[4];
+#if GB_WARP_SPMM
+          wbsr_row_d(a.m, a.m.hb, p, W, W, lane, I, act, acc);
+          if (lane >= W || !act) continue;
+#else
           bsr_row_d(a.m, a.m.hb, p, W, c, I, acc);
+#endif
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
             const size_t e = (size_t)(4 * I + rr) * W + c;
@@ -617,6 +633,49 @@ __global__ void __launch_bounds__(TPB, MIN_TEAMS_PER_SM) team_kernel(const __gri
     __syncthreads();
     if (sm.panel >= a.npanels) return;
     solve_panel<MIX>(a, sm, sx, ws, dyn_smem);
+    __syncthreads();
+  }
+}
+
+// Batched form: many independent systems (each with its own matrix, shifts,
+// columns and outputs) in one persistent launch.  Work items are (system,
+// panel) pairs numbered through panel_prefix (the host orders the systems,
+// largest first); a team copies the item's system descriptor into shared
+// memory and runs the same panel solver.  The team workspace is laid out for
+// the largest system.
+template <bool MIX>
+__global__ void __launch_bounds__(TPB, MIN_TEAMS_PER_SM)
+    team_kernel_batched(const Args* __restrict__ sys, const int* __restrict__ panel_prefix, int nsys,
+                        int* __restrict__ counter, char* team_ws, size_t team_bytes) {
+  __shared__ Smem sm;
+  __shared__ PanelSmemExtra sx;
+  __shared__ Args sa;
+  __shared__ int s_sys;
+  extern __shared__ __align__(16) char dyn_smem[];
+  char* ws = team_ws + (size_t)blockIdx.x * team_bytes;
+  const int total = panel_prefix[nsys];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = atomicAdd(counter, 1);
+      int lo = 0;
+      if (item < total) {
+        int hi = nsys;  // panel_prefix[lo] <= item < panel_prefix[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (panel_prefix[mid] <= item) lo = mid;
+          else hi = mid;
+        }
+      }
+      s_sys = item < total ? lo : -1;
+      sm.panel = item < total ? item - panel_prefix[lo] : 0;
+    }
+    __syncthreads();
+    if (s_sys < 0) return;
+    const unsigned* src = reinterpret_cast<const unsigned*>(sys + s_sys);
+    unsigned* dst = reinterpret_cast<unsigned*>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(Args) / sizeof(unsigned)); i += TPB) dst[i] = src[i];
+    __syncthreads();
+    solve_panel<MIX>(sa, sm, sx, ws, dyn_smem);
     __syncthreads();
   }
 }

@@ -55,6 +55,35 @@ namespace {
 template <bool F64>
 __global__ void spmm_kernel(const gbk::DevMat m, int which, int W, const void* __restrict__ xv,
                             void* __restrict__ yv) {
+  const int lane = threadIdx.x & 31;
+  if (W <= 8) {
+    // narrow panels: one warp per block row, lanes split the stored blocks
+    const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    int Wp = 1;
+    while (Wp < W) Wp <<= 1;
+    const int c = lane % Wp;
+    const bool active = c < W;
+    for (long long I = warp0; I < m.nb; I += nwarps) {
+      const int nrow = min(4, m.n - 4 * (int)I);
+      if constexpr (F64) {
+        double2 acc[4];
+        gbk::wbsr_row_d(m, which ? m.sb : m.hb, static_cast<const double2*>(xv), W, Wp, lane, (int)I, active, acc);
+        double2* y = static_cast<double2*>(yv);
+        if (lane < Wp && active)
+          for (int r = 0; r < nrow; ++r) y[(size_t)(4 * I + r) * W + c] = acc[r];
+      } else {
+        float2 acc[4];
+        gbk::wbsr_row_f(m, which ? m.sb_hi : m.hb_hi, static_cast<const float2*>(xv), W, Wp, lane, (int)I, active,
+                        acc);
+        float2* y = static_cast<float2*>(yv);
+        if (lane < Wp && active)
+          for (int r = 0; r < nrow; ++r) y[(size_t)(4 * I + r) * W + c] = acc[r];
+      }
+    }
+    return;
+  }
+  // wide panels: one thread per (block row, column), consecutive threads take consecutive columns
   const long long items = (long long)m.nb * W;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
@@ -246,9 +275,11 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
     GB_CUDA(cudaMemcpyAsync(pad, x, esz * m->n * w, cudaMemcpyDeviceToDevice, s));
     xin = pad;
   }
-  const long long items = (long long)m->nb * w;
   const int threads = 256;
-  const int blocks = (int)std::min<long long>((items + threads - 1) / threads, 152LL * 32);
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+  const long long work = w <= 8 ? (long long)m->nb * 32 : (long long)m->nb * w;  // threads of work
+  const int blocks = (int)std::min<long long>((work + threads - 1) / threads, (long long)nsm * 8);
   if (prec == GB_FP64)
     spmm_kernel<true><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
   else
@@ -665,5 +696,317 @@ gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, 
 }
 
 size_t gb_static_scratch_bytes(void) { return kStaticScratchBytes; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched solve
+// Many independent systems in one persistent launch (team_kernel_batched).
+namespace {
+
+// Team-workspace layout for the given maxima (same regions as a single solve).
+size_t layout_team(size_t N4, int W, int K, int KG, int maxit, int Mcap, bool want_g, gbk::Args& a) {
+  const size_t Kz = K, Wz = W, mx = maxit;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t vec = N4 * Wz * 16;
+  a.o_r = take(vec);
+  a.o_rt = take(vec);
+  a.o_p = take(vec);
+  a.o_sp = take(vec);
+  a.o_u = take(vec);
+  a.o_w = take(vec);
+  a.o_g = take(vec);
+  a.o_d = take(vec);
+  a.o_q = take(vec);
+  a.o_x = take(vec);
+  a.o_hr = take((mx + 1) * (size_t)Mcap * 16);
+  a.o_ab = take(mx * Wz * 2 * 16);
+  a.o_L = take((mx + 1) * Wz * sizeof(int));
+  a.o_t = take((mx + 1) * Wz * 16);
+  a.o_ck = take((mx / gbk::CK + 1) * Wz * Kz * 2 * 16);
+  a.o_pi = take(Wz * Kz * 2 * 16);
+  a.o_nk = take(Wz * Kz * sizeof(int));
+  a.o_res = take(Wz * Kz * sizeof(double));
+  a.o_buf = take((gbk::CK + 1) * Wz * Kz * 16);
+  a.o_cp = take((mx + 1) * Wz * KG * 2 * 16);
+  a.o_cf = take((mx + 1) * Wz * 2 * 16);
+  a.o_cg = want_g ? take((mx + 1) * Wz * Kz * 16) : 0;
+  return off;
+}
+
+struct BatchPlan {
+  int W, teams, total_panels, maxK, maxit, Mcap, KG;
+  bool mixed, want_g;
+  size_t N4, team_bytes, header_bytes, total;
+  std::vector<int> order;  // systems, largest estimated cost first
+  gbk::Args proto;
+};
+
+gb_status make_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                          const gb_outputs* outs, int32_t panel, BatchPlan* bp) {
+  if (nsys < 1 || !mats || !params) return fail(GB_EINVAL, "need nsys >= 1, mats and params");
+  const gb_precision prec = params[0].prec;
+  size_t n4max = 0;
+  int kmax = 0, itmax = 0, rowmax = 0, dev = -1;
+  long long cols = 0;
+  bool want_g = false;
+  for (int s = 0; s < nsys; ++s) {
+    Plan pl;
+    gb_status st = make_plan(mats[s], &params[s], false, &pl);
+    if (st != GB_OK) {
+      char msg[sizeof(gb::g_err)];
+      std::snprintf(msg, sizeof msg, "%s", gb::g_err);
+      return fail(st, "system %d: %s", s, msg);
+    }
+    if (params[s].prec != prec) return fail(GB_EINVAL, "all systems must use the same precision");
+    if (dev >= 0 && mats[s]->device != dev) return fail(GB_EINVAL, "all matrices must live on one device");
+    dev = mats[s]->device;
+    n4max = std::max(n4max, 4 * (size_t)mats[s]->nb);
+    kmax = std::max(kmax, (int)params[s].nshift);
+    itmax = std::max(itmax, (int)params[s].maxit);
+    rowmax = std::max(rowmax, (int)mats[s]->max_row);
+    cols += params[s].nrhs;
+    if (outs && outs[s].g_proj) want_g = true;
+  }
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  const int nsm = prop.multiProcessorCount;
+  const void* fn = prec == GB_FP64 ? (const void*)gbk::team_kernel_batched<false>
+                                   : (const void*)gbk::team_kernel_batched<true>;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gbk::TPB, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  int W = panel;
+  if (W <= 0) {  // widest panel that still gives every resident team a work item
+    W = 1;
+    for (int cand : {32, 16, 8, 4, 2}) {
+      long long np = 0;
+      for (int s = 0; s < nsys; ++s) np += (params[s].nrhs + cand - 1) / cand;
+      if (np >= (long long)nsm * per_sm) {
+        W = cand;
+        break;
+      }
+    }
+  }
+  if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32)
+    return fail(GB_EINVAL, "panel must be 1, 2, 4, 8, 16 or 32");
+  bp->W = W;
+  bp->mixed = prec == GB_MIXED;
+  bp->want_g = want_g;
+  bp->N4 = n4max;
+  bp->maxK = kmax;
+  bp->KG = (kmax + 31) / 32;
+  bp->maxit = itmax;
+  bp->Mcap = W * rowmax;
+  std::memset(&bp->proto, 0, sizeof bp->proto);
+  bp->team_bytes = layout_team(n4max, W, kmax, bp->KG, itmax, bp->Mcap, want_g, bp->proto);
+  bp->total_panels = 0;
+  for (int s = 0; s < nsys; ++s) bp->total_panels += (params[s].nrhs + W - 1) / W;
+  bp->teams = std::min(bp->total_panels, nsm * per_sm);
+  // largest systems first (cost ~ basis size x shifts) for load balance
+  bp->order.resize(nsys);
+  for (int s = 0; s < nsys; ++s) bp->order[s] = s;
+  std::stable_sort(bp->order.begin(), bp->order.end(), [&](int x, int y) {
+    return (double)mats[x]->n * params[x].nshift > (double)mats[y]->n * params[y].nshift;
+  });
+  // header: descriptors, panel prefix, counter, then per-system arrays
+  size_t hb = align256(sizeof(gbk::Args) * nsys) + align256(sizeof(int) * (nsys + 1)) + 256;
+  for (int s = 0; s < nsys; ++s)
+    hb += 3 * align256(16 * (size_t)params[s].nshift) + align256(sizeof(int) * params[s].nrhs) +
+          align256(sizeof(long long) * (params[s].nrhs + 1)) + align256(sizeof(int) * params[s].nrhs);
+  bp->header_bytes = hb;
+  bp->total = hb + bp->team_bytes * bp->teams + 256;
+  return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                 int32_t panel, int32_t want_g) {
+  clear_error();
+  BatchPlan bp;
+  std::vector<gb_outputs> fake;
+  if (want_g && nsys > 0) {
+    fake.assign(nsys, gb_outputs{});
+    for (auto& f : fake) f.g_proj = reinterpret_cast<double*>(1);
+  }
+  if (make_batch_plan(nsys, mats, params, want_g ? fake.data() : nullptr, panel, &bp) != GB_OK) return 0;
+  return bp.total;
+}
+
+gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                   const gb_outputs* outs, int32_t panel, void* workspace, size_t workspace_bytes,
+                                   void* stream) {
+  clear_error();
+  if (!outs) return fail(GB_EINVAL, "outputs is NULL");
+  BatchPlan bp;
+  gb_status st = make_batch_plan(nsys, mats, params, outs, panel, &bp);
+  if (st != GB_OK) return st;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < bp.total) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, bp.total);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != mats[0]->device) return fail(GB_EINVAL, "current device differs from the matrices' device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(workspace);
+  std::vector<char> hdr(bp.header_bytes, 0);
+  gbk::Args* desc = reinterpret_cast<gbk::Args*>(hdr.data());
+  size_t off = align256(sizeof(gbk::Args) * nsys);
+  int* prefix = reinterpret_cast<int*>(hdr.data() + off);
+  const size_t o_prefix = off;
+  off += align256(sizeof(int) * (nsys + 1));
+  const size_t o_counter = off;
+  off += 256;
+  std::vector<size_t> o_status(nsys);
+  prefix[0] = 0;
+  char* team_ws = wsb + align256(bp.header_bytes);
+  for (int q = 0; q < nsys; ++q) {
+    const int sidx = bp.order[q];
+    const gb_matrix* m = mats[sidx];
+    const gb_solve_params* p = &params[sidx];
+    const gb_outputs* out = &outs[sidx];
+    const int K = p->nshift, nrhs = p->nrhs;
+    const size_t o_z = off;
+    off += align256(16 * (size_t)K);
+    const size_t o_wr = off;
+    off += align256(16 * (size_t)K);
+    const size_t o_we = off;
+    off += align256(16 * (size_t)K);
+    const size_t o_cols = off;
+    off += align256(sizeof(int) * nrhs);
+    const size_t o_off = off;
+    off += align256(sizeof(long long) * (nrhs + 1));
+    o_status[sidx] = off;
+    off += align256(sizeof(int) * nrhs);
+    double2* hz = reinterpret_cast<double2*>(hdr.data() + o_z);
+    double2* hwr = reinterpret_cast<double2*>(hdr.data() + o_wr);
+    double2* hwe = reinterpret_cast<double2*>(hdr.data() + o_we);
+    for (int k = 0; k < K; ++k) {
+      hz[k] = make_double2(p->z_re[k], p->z_im[k]);
+      hwr[k] = p->w_rho ? make_double2(p->w_rho[2 * k], p->w_rho[2 * k + 1]) : make_double2(0, 0);
+      hwe[k] = p->w_edm ? make_double2(p->w_edm[2 * k], p->w_edm[2 * k + 1]) : make_double2(0, 0);
+    }
+    std::memcpy(hdr.data() + o_cols, p->rhs_cols, sizeof(int) * nrhs);
+    long long* ho = reinterpret_cast<long long*>(hdr.data() + o_off);
+    ho[0] = 0;
+    for (int i = 0; i < nrhs; ++i) {
+      const int j = p->rhs_cols[i];
+      ho[i + 1] = ho[i] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+    }
+    gbk::Args a = bp.proto;  // workspace regions laid out for the maxima
+    a.m = m->dm;
+    a.K = K;
+    a.W = bp.W;
+    a.KG = (K + 31) / 32;
+    a.nrhs = nrhs;
+    a.npanels = (nrhs + bp.W - 1) / bp.W;
+    a.maxit = p->maxit;
+    a.inner_maxit = 500;
+    a.has_rho = p->w_rho != nullptr;
+    a.has_edm = p->w_edm != nullptr;
+    a.want_g = out->g_proj != nullptr;
+    a.tol = p->tol;
+    a.itol = p->inner_tol > 0 ? p->inner_tol : (p->prec == GB_FP64 ? 1e-14 : 1e-7);
+    const int seed = p->seed_shift >= 0 ? p->seed_shift : K / 2;
+    a.sigma = make_double2(p->z_re[seed], p->z_im[seed]);
+    a.z = reinterpret_cast<const double2*>(wsb + o_z);
+    a.w_rho = reinterpret_cast<const double2*>(wsb + o_wr);
+    a.w_edm = reinterpret_cast<const double2*>(wsb + o_we);
+    a.rhs_cols = reinterpret_cast<const int*>(wsb + o_cols);
+    a.out_off = reinterpret_cast<const long long*>(wsb + o_off);
+    a.status = reinterpret_cast<int*>(wsb + o_status[sidx]);
+    a.panel_counter = reinterpret_cast<int*>(wsb + o_counter);
+    a.team_ws = team_ws;
+    a.team_bytes = bp.team_bytes;
+    a.Mcap = bp.W * m->max_row;
+    a.cg_smem = 0;
+    a.ldos = out->ldos;
+    a.rho = out->rho;
+    a.edm = out->edm;
+    a.q = out->q;
+    a.e_loc = out->e_loc;
+    a.iters = out->iters;
+    a.inner_iters = out->inner_iters;
+    a.col_status = out->col_status;
+    a.conv = out->converged;
+    a.resid = out->resid;
+    a.g_proj = reinterpret_cast<double2*>(out->g_proj);
+    a.P = ho[nrhs];
+    desc[q] = a;
+    prefix[q + 1] = prefix[q] + a.npanels;
+  }
+  GB_CUDA(cudaMemcpyAsync(wsb, hdr.data(), bp.header_bytes, cudaMemcpyHostToDevice, s));
+  const gbk::Args* d_desc = reinterpret_cast<const gbk::Args*>(wsb);
+  const int* d_prefix = reinterpret_cast<const int*>(wsb + o_prefix);
+  int* d_counter = reinterpret_cast<int*>(wsb + o_counter);
+  if (bp.mixed)
+    gbk::team_kernel_batched<true><<<bp.teams, gbk::TPB, 0, s>>>(d_desc, d_prefix, nsys, d_counter, team_ws,
+                                                                 bp.team_bytes);
+  else
+    gbk::team_kernel_batched<false><<<bp.teams, gbk::TPB, 0, s>>>(d_desc, d_prefix, nsys, d_counter, team_ws,
+                                                                  bp.team_bytes);
+  GB_CUDA(cudaGetLastError());
+  GB_CUDA(cudaMemcpyAsync(hdr.data(), wsb, bp.header_bytes, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  int any = 0;
+  for (int q = 0; q < nsys; ++q) {
+    const int* hs = reinterpret_cast<const int*>(hdr.data() + o_status[q]);
+    for (int i = 0; i < params[q].nrhs; ++i) any |= hs[i];
+  }
+  if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
+  if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
+  if (any & (gbk::kStNoConv | gbk::kStInner))
+    return fail(GB_ENOCONV, "some (shift, column) pairs did not reach tol within maxit%s",
+                (any & gbk::kStInner) ? " (inner CG hit its cap)" : "");
+  return GB_OK;
+}
+
+gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                const gb_outputs* outs, int32_t probe_maxit, void* workspace,
+                                size_t workspace_bytes, void* stream, int32_t* best_panel, float* times_ms) {
+  clear_error();
+  if (!best_panel || nsys < 1 || probe_maxit < 1) return fail(GB_EINVAL, "bad tuner arguments");
+  std::vector<gb_solve_params> probe(params, params + nsys);
+  for (auto& p : probe) p.maxit = std::min(p.maxit, probe_maxit);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  GB_CUDA(cudaEventCreate(&e0));
+  GB_CUDA(cudaEventCreate(&e1));
+  const int cands[4] = {4, 8, 16, 32};
+  float best = 1e30f;
+  *best_panel = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (times_ms) times_ms[i] = -1.f;
+    BatchPlan bp;
+    if (make_batch_plan(nsys, mats, probe.data(), outs, cands[i], &bp) != GB_OK || bp.total > workspace_bytes)
+      continue;
+    cudaEventRecord(e0, s);
+    const gb_status st = gb_shifted_solve_batched(nsys, mats, probe.data(), outs, cands[i], workspace,
+                                                  workspace_bytes, stream);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    if (st != GB_OK && st != GB_ENOCONV) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (times_ms) times_ms[i] = ms;
+    if (ms < best) {
+      best = ms;
+      *best_panel = cands[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  clear_error();
+  if (*best_panel == 0) return fail(GB_ENOMEM, "no candidate panel width fits the workspace");
+  return GB_OK;
+}
 
 }  // extern "C"

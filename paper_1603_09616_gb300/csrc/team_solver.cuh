@@ -160,18 +160,29 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* __restrict__ f, dou
     if (threadIdx.x == 0) ++sm.inner_count;
     {  // q = S d, d^T q
       double v[2] = {0, 0};
+#if GB_WARP_SPMM
+      const int lane = threadIdx.x & 31;
+      const bool act = sm.act[c] != 0;
+      for (int I = threadIdx.x >> 5; I < nb; I += NWARP) {
+        double2 acc[4];
+        wbsr_row_d(a.m, a.m.sb, d, W, W, lane, I, act, acc);
+        if (lane < W && act) {
+#else
       for (int it = threadIdx.x; it < nb * W; it += TPB) {
         if (!sm.act[c]) continue;
         const int I = it / W;
         double2 acc[4];
         bsr_row_d(a.m, a.m.sb, d, W, c, I, acc);
+        {
+#endif
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const size_t e = (size_t)(4 * I + r) * W + c;
-          const double2 dv = d[e];
-          q[e] = acc[r];
-          v[0] = fma(dv.x, acc[r].x, v[0]);
-          v[1] = fma(dv.y, acc[r].y, v[1]);
+          for (int r = 0; r < 4; ++r) {
+            const size_t e = (size_t)(4 * I + r) * W + c;
+            const double2 dv = d[e];
+            q[e] = acc[r];
+            v[0] = fma(dv.x, acc[r].x, v[0]);
+            v[1] = fma(dv.y, acc[r].y, v[1]);
+          }
         }
       }
       block_reduce<2>(v, W, sm.rs);
@@ -269,18 +280,29 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float
     {
       double v[2] = {0, 0};
       float v0 = 0.f, v1 = 0.f;
+#if GB_WARP_SPMM
+      const int lane = threadIdx.x & 31;
+      const bool act = sm.act[c] != 0;
+      for (int I = threadIdx.x >> 5; I < nb; I += NWARP) {
+        float2 acc[4];
+        wbsr_row_f(a.m, a.m.sb_hi, d, W, W, lane, I, act, acc);
+        if (lane < W && act) {
+#else
       for (int it = threadIdx.x; it < nb * W; it += TPB) {
         if (!sm.act[c]) continue;
         const int I = it / W;
         float2 acc[4];
         bsr_row_f(a.m, a.m.sb_hi, d, W, c, I, acc);
+        {
+#endif
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const size_t e = (size_t)(4 * I + r) * W + c;
-          const float2 dv = d[e];
-          q[e] = acc[r];
-          v0 = fmaf(dv.x, acc[r].x, v0);
-          v1 = fmaf(dv.y, acc[r].y, v1);
+          for (int r = 0; r < 4; ++r) {
+            const size_t e = (size_t)(4 * I + r) * W + c;
+            const float2 dv = d[e];
+            q[e] = acc[r];
+            v0 = fmaf(dv.x, acc[r].x, v0);
+            v1 = fmaf(dv.y, acc[r].y, v1);
+          }
         }
       }
       v[0] = v0;
@@ -417,11 +439,20 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
   {  // e = U - S x1 (float-float); w = x1; level 2 start: g = e, d = M^-1 e, x = 0
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
     // x1 is read by neighbouring block rows: write w first, then overwrite x after a barrier.
+#if GB_WARP_SPMM
+    const int lane = threadIdx.x & 31;
+    const bool act = sm.act[c] != 0;
+    for (int I = threadIdx.x >> 5; I < nb; I += NWARP) {
+      gbff::acc are[4], aim[4];
+      wbsr_row_ffx(a.m, a.m.sb_hi, a.m.sb_lo, x, W, W, lane, I, act, are, aim);
+      if (lane >= W || !act) continue;
+#else
     for (int it = threadIdx.x; it < nb * W; it += TPB) {
       if (!sm.act[c]) continue;
       const int I = it / W;
       gbff::acc are[4], aim[4];
       bsr_row_ffx(a.m, a.m.sb_hi, a.m.sb_lo, x, W, c, I, are, aim);
+#endif
       float2 ev[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
