@@ -72,6 +72,8 @@ typedef struct {
   int32_t block;      /* block size (4)                                       */
   int32_t device;     /* CUDA device ordinal holding the matrix               */
   int32_t reserved;
+  double s_lam_min;   /* extreme eigenvalues of M^-1 S, M the 4x4 block       */
+  double s_lam_max;   /* diagonal of S (Lanczos estimates at build time)      */
 } gb_matrix_info;
 
 /*
@@ -144,7 +146,9 @@ typedef struct {
                             (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level) */
   int32_t panel;         /* RHS columns per panel (1..32); <= 0: auto            */
   int32_t flags;         /* bit 1: keep the inner-CG vectors of a panel in shared
-                            memory when they fit (fewer teams per SM)           */
+                            memory when they fit (fewer teams per SM);
+                            bit 2: mixed path uses CG instead of the Chebyshev
+                            inner iteration for its FP32 levels              */
   int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
   int32_t reserved;
 } gb_solve_params;

@@ -48,7 +48,8 @@ class GBError(RuntimeError):
 
 class MatrixInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64), ("nnzb", C.c_int64),
-                ("max_row", C.c_int32), ("block", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32)]
+                ("max_row", C.c_int32), ("block", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32),
+                ("s_lam_min", C.c_double), ("s_lam_max", C.c_double)]
 
 
 class SolveParams(C.Structure):

@@ -148,4 +148,121 @@ gb_status build_host_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_i
   return GB_OK;
 }
 
+// Extreme eigenvalues of M^-1 S (M = block diagonal of S) by Lanczos on the
+// symmetric similar operator T = L^-1 S L^-T (M = L L^T per 4x4 block), then
+// bisection on the Sturm count of the tridiagonal matrix.  These bounds set
+// the Chebyshev inner iteration of the mixed path.
+void preconditioned_s_bounds(HostBSR* hb) {
+  const int64_t nb = hb->nb, n4 = 4 * nb;
+  // Cholesky factors of the diagonal blocks: minv = L^-T L^-1, so recover L^-1
+  // from the diagonal blocks directly.
+  std::vector<double> linv(nb * 16, 0.0);
+  for (int64_t I = 0; I < nb; ++I) {
+    const int32_t b0 = hb->blk_ptr[I], b1 = hb->blk_ptr[I + 1];
+    const int32_t* f = std::lower_bound(hb->blk_col.data() + b0, hb->blk_col.data() + b1, (int32_t)I);
+    double a[16], l[16] = {0};
+    std::memcpy(a, hb->blk_s.data() + (f - hb->blk_col.data()) * 16, sizeof a);
+    for (int r = 0; r < 4; ++r)
+      if (4 * I + r >= hb->n) a[r * 4 + r] = 1.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double v = a[i * 4 + j];
+        for (int k = 0; k < j; ++k) v -= l[i * 4 + k] * l[j * 4 + k];
+        l[i * 4 + j] = (i == j) ? std::sqrt(v) : v / l[j * 4 + j];
+      }
+    double* li = linv.data() + I * 16;
+    for (int i = 0; i < 4; ++i) {
+      li[i * 4 + i] = 1.0 / l[i * 4 + i];
+      for (int j = 0; j < i; ++j) {
+        double v = 0.0;
+        for (int k = j; k < i; ++k) v += l[i * 4 + k] * li[k * 4 + j];
+        li[i * 4 + j] = -v / l[i * 4 + i];
+      }
+    }
+  }
+  auto apply_T = [&](const std::vector<double>& v, std::vector<double>& out, std::vector<double>& tmp) {
+    // tmp = L^-T v, out = S tmp, out = L^-1 out (per block)
+    for (int64_t I = 0; I < nb; ++I)
+      for (int r = 0; r < 4; ++r) {
+        double acc = 0.0;
+        for (int t = 0; t < 4; ++t) acc += linv[I * 16 + t * 4 + r] * v[4 * I + t];
+        tmp[4 * I + r] = acc;
+      }
+    for (int64_t I = 0; I < nb; ++I) {
+      double acc[4] = {0, 0, 0, 0};
+      for (int32_t b = hb->blk_ptr[I]; b < hb->blk_ptr[I + 1]; ++b) {
+        const int32_t J = hb->blk_col[b];
+        const double* blk = hb->blk_s.data() + (size_t)b * 16;
+        for (int r = 0; r < 4; ++r)
+          for (int t = 0; t < 4; ++t) acc[r] += blk[r * 4 + t] * tmp[4 * J + t];
+      }
+      for (int r = 0; r < 4; ++r) {
+        double v2 = 0.0;
+        for (int t = 0; t <= r; ++t) v2 += linv[I * 16 + r * 4 + t] * acc[t];
+        out[4 * I + r] = (4 * I + r < hb->n) ? v2 : 0.0;
+      }
+    }
+  };
+  const int steps = (int)std::min<int64_t>(60, std::max<int64_t>(2, hb->n));
+  std::vector<double> v(n4, 0.0), vp(n4, 0.0), w(n4), tmp(n4);
+  uint64_t st = 0x9E3779B97F4A7C15ull;  // deterministic start vector
+  double nrm = 0.0;
+  for (int64_t i = 0; i < hb->n; ++i) {
+    st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+    v[i] = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+    nrm += v[i] * v[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (auto& x : v) x /= nrm;
+  std::vector<double> alpha, beta;
+  double bprev = 0.0;
+  for (int j = 0; j < steps; ++j) {
+    apply_T(v, w, tmp);
+    for (int64_t i = 0; i < n4; ++i) w[i] -= bprev * vp[i];
+    double al = 0.0;
+    for (int64_t i = 0; i < n4; ++i) al += w[i] * v[i];
+    for (int64_t i = 0; i < n4; ++i) w[i] -= al * v[i];
+    double bn = 0.0;
+    for (int64_t i = 0; i < n4; ++i) bn += w[i] * w[i];
+    bn = std::sqrt(bn);
+    alpha.push_back(al);
+    if (bn < 1e-12 || j == steps - 1) break;
+    beta.push_back(bn);
+    for (int64_t i = 0; i < n4; ++i) {
+      vp[i] = v[i];
+      v[i] = w[i] / bn;
+    }
+    bprev = bn;
+  }
+  const int m = (int)alpha.size();
+  auto count_below = [&](double x) {  // Sturm count of eigenvalues < x
+    int c = 0;
+    double q = alpha[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      const double qq = (q == 0.0) ? 1e-300 : q;
+      q = alpha[i] - x - beta[i - 1] * beta[i - 1] / qq;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(beta[i]) : 0.0);
+    lo = std::min(lo, alpha[i] - r);
+    hi = std::max(hi, alpha[i] + r);
+  }
+  auto bisect = [&](int k) {  // k-th smallest eigenvalue of the tridiagonal matrix
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (count_below(mid) > k) b = mid;
+      else a = mid;
+    }
+    return 0.5 * (a + b);
+  };
+  hb->lam_min = bisect(0);
+  hb->lam_max = bisect(m - 1);
+}
+
 }  // namespace gb

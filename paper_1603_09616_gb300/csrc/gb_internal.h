@@ -21,11 +21,13 @@ struct HostBSR {
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col_idx;
   std::vector<double> h_val, s_val;
+  double lam_min = 0.0, lam_max = 0.0;  // spectrum bounds of M^-1 S (block Jacobi M)
 };
 
 gb_status validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
                        const double* s);
 gb_status build_host_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
                          const double* s, HostBSR* out);
+void preconditioned_s_bounds(HostBSR* hb);
 
 }  // namespace gb

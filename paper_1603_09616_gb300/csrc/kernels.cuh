@@ -54,6 +54,7 @@ struct DevMat {
   const int* col_idx;
   const double* h_val;
   const double* s_val;
+  double s_lam_min, s_lam_max;  // spectrum bounds of the block-Jacobi-preconditioned S
 };
 
 // ------------------------------------------------------------ complex FP64

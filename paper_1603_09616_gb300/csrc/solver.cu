@@ -140,6 +140,7 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   HostBSR hb;
   gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
   if (st != GB_OK) return st;
+  preconditioned_s_bounds(&hb);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
   GB_CUDA(cudaGetDevice(&dev));
@@ -230,6 +231,8 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   d.col_idx = reinterpret_cast<const int*>(b + o_ci);
   d.h_val = reinterpret_cast<const double*>(b + o_hv);
   d.s_val = reinterpret_cast<const double*>(b + o_sv);
+  d.s_lam_min = hb.lam_min;
+  d.s_lam_max = hb.lam_max;
   *out = m;
   return GB_OK;
 }
@@ -245,6 +248,8 @@ gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info) {
   info->block = 4;
   info->device = m->device;
   info->reserved = 0;
+  info->s_lam_min = m->dm.s_lam_min;
+  info->s_lam_max = m->dm.s_lam_max;
   return GB_OK;
 }
 
@@ -294,6 +299,32 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
 
 // ------------------------------------------------------------ shifted solve
 namespace {
+
+// Inner solver of the mixed path: Chebyshev (default) when the spectrum bounds
+// of the preconditioned S are known and positive, CG when flags bit 2 asks for
+// it.  K steps reduce the preconditioned residual below itol by the Chebyshev
+// bound 2 sqrt(kappa) q^K (q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1)), with
+// the Lanczos bounds widened by 2% on each side.
+void set_inner_method(const gb_matrix* m, const gb_solve_params* p, double itol, gbk::Args& a) {
+  std::memset(&a, 0, sizeof a);
+  const double lmin = m->dm.s_lam_min * 0.98, lmax = m->dm.s_lam_max * 1.02;
+  if (p->prec != GB_MIXED || (p->flags & 4) || !(lmin > 0.0) || !(lmax > lmin)) return;
+  const double kappa = lmax / lmin, sk = std::sqrt(kappa);
+  const double q = (sk - 1.0) / (sk + 1.0);
+  int K = (int)std::ceil(std::log(2.0 * sk / itol) / std::log(1.0 / q));
+  K = std::max(1, std::min(K, 48));
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < K; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    a.cheb_A[k] = (float)(rn * rho);
+    a.cheb_B[k] = (float)(2.0 * rn / delta);
+    rho = rn;
+  }
+  a.cheb_c0 = (float)(1.0 / theta);
+  a.cheb_K = K;
+  a.inner_cheb = 1;
+}
 
 struct Plan {
   int W, KG, npanels, teams, teams_per_sm, Mcap, inner_maxit, cg_smem;
@@ -349,10 +380,13 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   };
   int W = p->panel;
   if (W <= 0) {
+    // one wave that fills >= 3/4 of the team slots beats 1.5 waves of half-size
+    // panels (measured on the 1900-orbital chain: W = 8, 238 panels on 304
+    // slots, ~20% faster than W = 4)
     W = 1;
     for (int cand : {32, 16, 8, 4, 2}) {
       const size_t dyn = fits(cand) ? 3 * n4 * (size_t)cand * cg_esz : 0;
-      if ((p->nrhs + cand - 1) / cand >= nsm * occupancy(dyn)) {
+      if (4LL * ((p->nrhs + cand - 1) / cand) >= 3LL * nsm * occupancy(dyn)) {
         W = cand;
         break;
       }
@@ -378,6 +412,7 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   else
     pl->itol = p->inner_tol > 0 ? p->inner_tol : 1e-7;
 
+  set_inner_method(m, p, pl->itol, pl->a);
   const size_t K = p->nshift, Wz = W, maxit = p->maxit, N4 = 4 * (size_t)m->nb;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -386,7 +421,6 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
     return o;
   };
   gbk::Args& a = pl->a;
-  std::memset(&a, 0, sizeof a);
   const size_t vec = N4 * Wz * 16;
   a.o_r = take(vec);
   a.o_rt = take(vec);
@@ -787,7 +821,7 @@ gb_status make_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_s
     for (int cand : {32, 16, 8, 4, 2}) {
       long long np = 0;
       for (int s = 0; s < nsys; ++s) np += (params[s].nrhs + cand - 1) / cand;
-      if (np >= (long long)nsm * per_sm) {
+      if (4 * np >= 3LL * nsm * per_sm) {
         W = cand;
         break;
       }
@@ -902,6 +936,15 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
       ho[i + 1] = ho[i] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
     }
     gbk::Args a = bp.proto;  // workspace regions laid out for the maxima
+    {
+      gbk::Args im;
+      set_inner_method(m, p, p->inner_tol > 0 ? p->inner_tol : (p->prec == GB_FP64 ? 1e-14 : 1e-7), im);
+      a.inner_cheb = im.inner_cheb;
+      a.cheb_K = im.cheb_K;
+      a.cheb_c0 = im.cheb_c0;
+      std::memcpy(a.cheb_A, im.cheb_A, sizeof a.cheb_A);
+      std::memcpy(a.cheb_B, im.cheb_B, sizeof a.cheb_B);
+    }
     a.m = m->dm;
     a.K = K;
     a.W = bp.W;

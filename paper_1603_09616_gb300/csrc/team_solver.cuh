@@ -56,6 +56,11 @@ struct Args {
   size_t o_hr, o_ab, o_L, o_t, o_ck, o_pi, o_nk, o_res, o_buf, o_cp, o_cf, o_cg;
   int Mcap;
   int cg_smem;  // 1: the inner-CG vectors g, d, q live in dynamic shared memory
+  // Chebyshev inner iteration of the mixed path (inner_cheb = 1): K steps per
+  // FP32 level with d_{k+1} = A_k d_k + B_k M^-1 r_{k+1}, d_0 = c0 M^-1 r_0.
+  int inner_cheb, cheb_K;
+  float cheb_c0;
+  float cheb_A[48], cheb_B[48];
   double* ldos;
   double* rho;
   double* edm;
@@ -384,6 +389,57 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float
   }
 }
 
+// ------------------------------------------------------------ inner Chebyshev, FP32
+// Chebyshev semi-iteration on the block-Jacobi-preconditioned S (spectrum
+// bounds from gb_build_bsr) for x (= 0 on entry), r (= rhs), d_0 (= c0 M^-1 r)
+// already set: K fused steps, one barrier each, no reductions.
+__device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ r,
+                            float2* __restrict__ dA, float2* __restrict__ dB) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  for (int k = 0; k < a.cheb_K; ++k) {
+    const float Ak = a.cheb_A[k], Bk = a.cheb_B[k];
+    const bool last = k + 1 == a.cheb_K;
+    const float2* __restrict__ dk = (k & 1) ? dB : dA;
+    float2* __restrict__ dn = (k & 1) ? dA : dB;
+    for (int it = threadIdx.x; it < nb * W; it += TPB) {
+      if (!sm.act[c]) continue;
+      const int I = it / W;
+      float2 acc[4];
+      bsr_row_f(a.m, a.m.sb_hi, dk, W, c, I, acc);
+      float2 rv[4], dv[4];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const size_t e = (size_t)(4 * I + rr) * W + c;
+        dv[rr] = dk[e];
+        float2 xv = x[e];
+        xv.x += dv[rr].x;
+        xv.y += dv[rr].y;
+        x[e] = xv;
+        float2 g = r[e];
+        g.x -= acc[rr].x;
+        g.y -= acc[rr].y;
+        r[e] = g;
+        rv[rr] = g;
+      }
+      if (last) continue;
+      const float4* Mi = reinterpret_cast<const float4*>(a.m.minv32 + (size_t)I * 16);
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const float4 mr = __ldg(Mi + rr);
+        float2 zr;
+        zr.x = mr.x * rv[0].x + mr.y * rv[1].x + mr.z * rv[2].x + mr.w * rv[3].x;
+        zr.y = mr.x * rv[0].y + mr.y * rv[1].y + mr.z * rv[2].y + mr.w * rv[3].y;
+        float2 nd;
+        nd.x = fmaf(Ak, dv[rr].x, Bk * zr.x);
+        nd.y = fmaf(Ak, dv[rr].y, Bk * zr.y);
+        dn[(size_t)(4 * I + rr) * W + c] = nd;
+      }
+    }
+    if (threadIdx.x == 0) ++sm.inner_count;
+    __syncthreads();
+  }
+}
+
 // Stores the per-real-column CG start scalars from a reduced {g^T z, ||f||^2}.
 __device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
   if (threadIdx.x < 2 * W) {
@@ -423,7 +479,7 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
         zr.y = mr.x * gv[0].y + mr.y * gv[1].y + mr.z * gv[2].y + mr.w * gv[3].y;
         const size_t e = (size_t)(4 * I + r) * W + c;
         g[e] = gv[r];
-        d[e] = zr;
+        d[e] = a.inner_cheb ? make_float2(a.cheb_c0 * zr.x, a.cheb_c0 * zr.y) : zr;
         x[e] = make_float2(0.f, 0.f);
         f0 = fmaf(gv[r].x, zr.x, f0);
         f1 = fmaf(gv[r].y, zr.y, f1);
@@ -435,7 +491,10 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     block_reduce<4>(v, W, sm.rs);
     cg_start_scalars(sm, W);
   }
-  cg32_loop(a, sm, x, g, d, q, itol);
+  if (a.inner_cheb)
+    cheb32_loop(a, sm, x, g, d, q);
+  else
+    cg32_loop(a, sm, x, g, d, q, itol);
   {  // e = U - S x1 (float-float); w = x1; level 2 start: g = e, d = M^-1 e, x = 0
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
     // x1 is read by neighbouring block rows: write w first, then overwrite x after a barrier.
@@ -470,7 +529,7 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
         float2 zr;
         zr.x = mr.x * ev[0].x + mr.y * ev[1].x + mr.z * ev[2].x + mr.w * ev[3].x;
         zr.y = mr.x * ev[0].y + mr.y * ev[1].y + mr.z * ev[2].y + mr.w * ev[3].y;
-        d[(size_t)(4 * I + r) * W + c] = zr;
+        d[(size_t)(4 * I + r) * W + c] = a.inner_cheb ? make_float2(a.cheb_c0 * zr.x, a.cheb_c0 * zr.y) : zr;
         f0 = fmaf(ev[r].x, zr.x, f0);
         f1 = fmaf(ev[r].y, zr.y, f1);
         f2 = fmaf(ev[r].x, ev[r].x, f2);
@@ -487,7 +546,10 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     }
     cg_start_scalars(sm, W);  // its barrier orders the x / w writes too
   }
-  cg32_loop(a, sm, x, g, d, q, itol);
+  if (a.inner_cheb)
+    cheb32_loop(a, sm, x, g, d, q);
+  else
+    cg32_loop(a, sm, x, g, d, q, itol);
   for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
     if (!sm.act[c]) continue;
     const float4 wv = w[e];

@@ -68,12 +68,12 @@ def test_chain800_fp64_sampled_columns():
 def test_ppv1900_mixed_sampled_vs_oracle_and_fp64(ppv):
     wl, mat, cols, ref = ppv
     mixed = gbg.shifted_solve(mat, wl["z"], cols, tol=wl["tol"], maxit=wl["maxit"], prec="mixed",
-                              w_rho=wl["w_rho"], w_edm=wl["w_edm"], want_g=True)
+                              w_rho=wl["w_rho"], w_edm=wl["w_edm"], want_g=True, inner_tol=wl["inner_tol"])
     assert mixed["status"] == 0, mixed["message"]
     for key in ("ldos", "rho", "edm", "q", "e_loc"):
         assert rel(to_np(mixed[key]), ref[key]) < 1e-6, key
     assert rel(to_np(mixed["g_proj"]), ref["g_proj"]) < 1e-6
-    fp64 = gbg.shifted_solve(mat, wl["z"], cols, tol=wl["tol"], maxit=wl["maxit"], prec="fp64",
+    fp64 = gbg.shifted_solve(mat, wl["z"], cols, tol=1e-10, maxit=30000, prec="fp64",
                              w_rho=wl["w_rho"], w_edm=wl["w_edm"])
     assert fp64["status"] == 0, fp64["message"]
     for key in ("ldos", "rho", "edm", "q", "e_loc"):
@@ -85,7 +85,7 @@ def test_ppv1900_full_launch(ppv):
     system, z = wl["system"], wl["z"]
     all_cols = np.arange(system.n, dtype=np.int32)
     out = gbg.shifted_solve(mat, z, all_cols, tol=wl["tol"], maxit=wl["maxit"], prec="mixed",
-                            w_rho=wl["w_rho"], w_edm=wl["w_edm"])
+                            w_rho=wl["w_rho"], w_edm=wl["w_edm"], inner_tol=wl["inner_tol"])
     assert out["status"] == 0, out["message"]
     assert to_np(out["converged"]).all()
     # sampled columns of the full launch against the oracle
