@@ -1,8 +1,9 @@
 """Build the in-tree CUDA library ``libgbgreen.so`` for sm_103a (GB300).
 
-Two translation units: ``csrc/solver.cu`` (kernels + C ABI, nvcc) and
-``csrc/bsr_build.cpp`` (host CSR -> 4x4 block builder, g++), compiled in
-parallel and linked with nvcc into ``paper_1603_09616_gb300/libgbgreen.so``.
+Three translation units: ``csrc/solver.cu`` (solver kernels + C ABI),
+``csrc/surrogate.cu`` (descriptor and MLP kernels) and ``csrc/bsr_build.cpp``
+(host CSR -> 4x4 block builder), compiled in parallel and linked with nvcc
+into ``paper_1603_09616_gb300/libgbgreen.so``.
 """
 from __future__ import annotations
 
@@ -34,10 +35,12 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     obj_cu = os.path.join(bdir, "solver.o")
+    obj_sg = os.path.join(bdir, "surrogate.o")
     obj_cpp = os.path.join(bdir, "bsr_build.o")
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
     cmds = [
         [nvcc, ARCH, "-lineinfo", *common, "-c", os.path.join(CSRC, "solver.cu"), "-o", obj_cu],
+        [nvcc, ARCH, "-lineinfo", *common, "-c", os.path.join(CSRC, "surrogate.cu"), "-o", obj_sg],
         [nvcc, *common, "-c", os.path.join(CSRC, "bsr_build.cpp"), "-o", obj_cpp],
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
@@ -48,7 +51,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         if p.returncode != 0:
             raise RuntimeError(f"build step failed: {' '.join(c)}\n{out}")
     tmp = LIB + ".tmp"
-    link = [nvcc, ARCH, "-shared", "-o", tmp, obj_cu, obj_cpp, "-lcudart"]
+    link = [nvcc, ARCH, "-shared", "-o", tmp, obj_cu, obj_sg, obj_cpp, "-lcudart"]
     res = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{res.stdout}")

@@ -47,6 +47,10 @@ struct gb_matrix {
   gbk::DevMat dm{};
 };
 
+namespace gb {
+const gbk::DevMat* devmat_of(const gb_matrix* m) { return &m->dm; }
+}  // namespace gb
+
 using namespace gb;
 
 // ------------------------------------------------------------ standalone SpMM

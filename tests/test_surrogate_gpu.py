@@ -1,0 +1,107 @@
+"""Surrogate kernels against the CPU references, and the surrogate end to end.
+
+* descriptor kernel vs oracle/descriptors.py on a small bundle
+* MLP forward / backward / Adam kernels vs oracle/mlp.py (same bf16 weights)
+* training on solver-generated (q, E) labels of small bundles, then inference
+  on a fresh bundle judged by the solver: the trained network must beat the
+  method without it (predicting the training mean) and the judged outputs
+  must agree with a full solve on the re-solved orbitals exactly.
+"""
+import numpy as np
+import pytest
+
+from oracle import descriptors as odesc
+from oracle import mlp as omlp
+from synth import fermi_weights, ppv_bundle, shift_grid
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+gbg = pytest.importorskip("paper_1603_09616_gb300")
+from paper_1603_09616_gb300 import surrogate as sg  # noqa: E402
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def test_descriptor_kernel_matches_oracle():
+    torch.cuda.set_device(0)
+    system = ppv_bundle(n_side=2, n_mono=3, seed=7)
+    mat = gbg.Matrix(system)
+    d = sg.descriptors(mat, system).cpu().numpy()
+    ref = odesc.descriptors(system, (system.atom_norb == 1).astype(int))
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-3)
+    assert np.max(np.abs(d - ref) / scale) < 2e-4
+    mat.close()
+
+
+def test_mlp_kernels_match_oracle():
+    torch.cuda.set_device(0)
+    net = sg.MLP(seed=3)
+    rng = np.random.default_rng(5)
+    for l in range(4):  # non-trivial biases
+        net.b[l].copy_(torch.as_tensor(rng.normal(0, 0.1, net.b[l].shape).astype(np.float32)))
+    B = 37
+    X = rng.normal(size=(B, 64)).astype(np.float32)
+    dY = rng.normal(size=(B, 2)).astype(np.float32)
+    Xt = torch.as_tensor(X).cuda()
+    Y = net.forward(Xt).cpu().numpy()
+    W, b = net.numpy_params()
+    yref, cache = omlp.forward(W, b, X)
+    assert rel(Y, yref) < 1e-4
+    net.backward(Xt, torch.as_tensor(dY).cuda())
+    gw, gb = omlp.backward(W, cache, dY)
+    for l in range(4):
+        assert rel(net.gw[l].cpu().numpy(), gw[l]) < 1e-4, l
+        assert rel(net.gb[l].cpu().numpy(), gb[l]) < 1e-4, l
+    # one Adam step, fed the kernel's own gradient so that only the update is compared
+    lib = sg._lib()
+    w0 = [w.copy() for w in W]
+    g_dev = [g.cpu().numpy().astype(np.float64) for g in net.gw]
+    import ctypes as C
+    sg._check(lib.gb_mlp_adam(C.byref(net._s), 1e-2, 0.9, 0.999, 1e-8, 1, None))
+    for l in range(4):
+        ref, _, _ = omlp.adam(w0[l].astype(np.float64), g_dev[l], 0, 0, 1e-2, 0.9, 0.999, 1e-8, 1)
+        assert rel(net.w[l].cpu().numpy(), ref) < 1e-5, l
+
+
+def test_training_reduces_loss_on_smooth_target():
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    X = torch.as_tensor(rng.normal(size=(8192, 64)).astype(np.float32)).cuda()
+    Y = torch.stack([torch.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2], torch.tanh(X[:, 3] - X[:, 4])], dim=1).contiguous()
+    sur = sg.Surrogate(seed=1)
+    hist = sur.fit(X, Y, epochs=30, batch=1024, lr=3e-3)
+    assert hist[-1] < 0.1 * hist[0]
+
+
+def test_surrogate_with_judge_on_fresh_bundle():
+    torch.cuda.set_device(0)
+    z = shift_grid(-15.0, 10.0, 48, 0.2)
+    w_rho, w_edm = fermi_weights(z)
+    train = [ppv_bundle(n_side=2, n_mono=4, seed=100 + s) for s in range(6)]
+    mats = [gbg.Matrix(s) for s in train]
+    labels = sg.solve_local_outputs(mats, train, z, w_rho, w_edm, tol=1e-6, maxit=4000)
+    X = torch.cat([sg.descriptors(m, s) for m, s in zip(mats, train)])
+    Y = torch.cat([torch.stack([q.float(), e.float()], dim=1) for q, e in labels]).contiguous()
+    sur = sg.Surrogate(seed=2)
+    sur.fit(X, Y, epochs=60, batch=512, lr=2e-3)
+    fresh = ppv_bundle(n_side=2, n_mono=4, seed=999)
+    mf = gbg.Matrix(fresh)
+    q, e, rep = sg.infer_with_judge(sur, mf, fresh, z, w_rho, w_edm, tol=1e-6, maxit=4000, sample_frac=0.05,
+                                    threshold=5e-2)
+    full = gbg.shifted_solve(mf, z, np.arange(fresh.n, dtype=np.int32), tol=1e-6, maxit=4000, prec="mixed",
+                             w_rho=w_rho, w_edm=w_edm)
+    qf, ef = full["q"].cpu().numpy(), full["e_loc"].cpu().numpy()
+    pred = sur.predict(sg.descriptors(mf, fresh)).cpu().numpy()
+    mae_net = np.abs(pred[:, 0] - qf).mean()
+    mae_mean = np.abs(Y[:, 0].mean().item() - qf).mean()
+    assert mae_net < 0.5 * mae_mean, (mae_net, mae_mean)
+    # re-solved orbitals carry the solver's values
+    qn = q.cpu().numpy()
+    assert rep["resolved"] >= rep["sample"] >= 1
+    if not rep["fell_back"]:
+        assert np.count_nonzero(np.isclose(qn, qf, rtol=0, atol=1e-9)) >= rep["resolved"]
+    for m in mats + [mf]:
+        m.close()
