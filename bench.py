@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-spmm", action="store_true", help="skip the bundle-scale SpMM bandwidth measurement")
+    ap.add_argument("--spmm-only", type=str, default="",
+                    help="comma-separated panel widths: only the bundle SpMM bandwidth measurement")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="measure the learned surrogate with solver judge instead of the solver step")
     ap.add_argument("--maxit", type=int, default=0, help="override the workload's iteration cap")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one solve of the workload (for ncu captures) and exit")
@@ -399,6 +403,70 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_surrogate(args):
+    """Surrogate (q, E) outputs/s with the solver as judge vs the plain solver.
+
+    Labels: the batched mixed solver on 24 seeded 2x2-chain x 6-monomer bundles
+    (912 orbitals each, 48 shifts on [-15, 10] eV + 0.2i, tol 1e-6).  Inference:
+    a fresh 3x3 x 10-monomer bundle (3,420 orbitals): descriptors, MLP, 5%
+    random re-solve plus out-of-range fallback, versus solving every orbital.
+    """
+    import torch
+
+    import paper_1603_09616_gb300 as gbg
+    from paper_1603_09616_gb300 import surrogate as sg
+    from synth import fermi_weights, ppv_bundle, shift_grid
+
+    torch.cuda.set_device(0)
+    z = shift_grid(-15.0, 10.0, 48, 0.2)
+    w_rho, w_edm = fermi_weights(z)
+    train = [ppv_bundle(n_side=2, n_mono=6, seed=1000 + s) for s in range(24)]
+    mats = [gbg.Matrix(s) for s in train]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    labels = sg.solve_local_outputs(mats, train, z, w_rho, w_edm, tol=1e-6, maxit=6000)
+    torch.cuda.synchronize()
+    t_labels = time.perf_counter() - t0
+    X = torch.cat([sg.descriptors(m, s) for m, s in zip(mats, train)])
+    Y = torch.cat([torch.stack([q.float(), e.float()], dim=1) for q, e in labels]).contiguous()
+    sur = sg.Surrogate(seed=0)
+    t0 = time.perf_counter()
+    hist = sur.fit(X, Y, epochs=80, batch=1024, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    fresh = ppv_bundle(n_side=3, n_mono=10, seed=4242)
+    mf = gbg.Matrix(fresh)
+    cols = np.arange(fresh.n, dtype=np.int32)
+    gbg.shifted_solve(mf, z, cols[:64], tol=1e-6, maxit=6000, prec="mixed", w_rho=w_rho, w_edm=w_edm)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full = gbg.shifted_solve(mf, z, cols, tol=1e-6, maxit=6000, prec="mixed", w_rho=w_rho, w_edm=w_edm)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    q, e, rep = sg.infer_with_judge(sur, mf, fresh, z, w_rho, w_edm, tol=1e-6, maxit=6000, sample_frac=0.05,
+                                    threshold=1e-3)
+    qf, ef = full["q"].cpu().numpy(), full["e_loc"].cpu().numpy()
+    pred = sur.predict(sg.descriptors(mf, fresh)).cpu().numpy()
+    qn, en = q.cpu().numpy(), e.cpu().numpy()
+    res = {
+        "metric": "surrogate local outputs (q_j, E_j) per second with the shifted solver as judge",
+        "value": fresh.n / rep["t_total_s"], "unit": "orbitals/s", "n_gpus": 1, "higher_is_better": True,
+        "plain_solver": {"value": fresh.n / t_plain, "unit": "orbitals/s", "seconds": t_plain},
+        "speedup_vs_plain": t_plain / rep["t_total_s"],
+        "network_mae": {"q": float(np.abs(pred[:, 0] - qf).mean()), "E": float(np.abs(pred[:, 1] - ef).mean())},
+        "mean_predictor_mae": {"q": float(np.abs(Y[:, 0].mean().item() - qf).mean()),
+                               "E": float(np.abs(Y[:, 1].mean().item() - ef).mean())},
+        "judged_output_mae": {"q": float(np.abs(qn - qf).mean()), "E": float(np.abs(en - ef).mean())},
+        "judged_output_max_err": {"q": float(np.abs(qn - qf).max()), "E": float(np.abs(en - ef).max())},
+        "judge": rep, "train": {"samples": int(X.shape[0]), "label_seconds": t_labels, "train_seconds": t_train,
+                                "loss_first": hist[0], "loss_last": hist[-1]},
+        "config": {"workload": "surrogate: train 24 x (2x2 chains x 6 monomers, 912 orbitals), infer 3x3 x 10 "
+                               "(3420 orbitals); 48 shifts on [-15,10] eV + 0.2i; judge 5% + out-of-range"},
+        "dtype": "bf16 weights, f32 accumulation", "data": "synthetic",
+    }
+    print(json.dumps(res), flush=True)
+
+
 def run_profile_case(args):
     """One gb_shifted_solve of the workload (short with --maxit), for ncu."""
     import torch
@@ -419,8 +487,17 @@ def run_profile_case(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.profile_case:
+    if a.spmm_only:
+        import torch
+
+        import paper_1603_09616_gb300 as gbg
+
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_spmm(gbg, torch, widths=tuple(int(w) for w in a.spmm_only.split(",")))))
+    elif a.profile_case:
         run_profile_case(a)
+    elif a.surrogate:
+        run_surrogate(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

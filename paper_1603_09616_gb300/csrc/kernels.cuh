@@ -285,7 +285,40 @@ __device__ __forceinline__ void wbsr_row_f(const DevMat& m, const float* __restr
   const int S = 32 / Wp, s = lane / Wp, c = lane - s * Wp;
   if (active) {
     const int b1 = m.blk_ptr[I + 1];
-    for (int b = m.blk_ptr[I] + s; b < b1; b += S) {
+    int b = m.blk_ptr[I] + s;
+    // groups of four blocks per lane: all block columns first, then every
+    // matrix and x load of the group, then the FMAs (four times the loads in
+    // flight of a block-at-a-time loop)
+    for (; b + 3 * S < b1; b += 4 * S) {
+      int J[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) J[u] = __ldg(m.blk_col + b + u * S);
+      float4 a[4][4];
+      float2 xv[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4* ab = reinterpret_cast<const float4*>(A + (size_t)(b + u * S) * 16);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[u][r] = __ldg(ab + r);
+        const float2* xr = x + (size_t)(4 * J[u]) * W + c;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) xv[u][t] = xr[(size_t)t * W];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          acc[r].x = fmaf(a[u][r].x, xv[u][0].x, acc[r].x);
+          acc[r].y = fmaf(a[u][r].x, xv[u][0].y, acc[r].y);
+          acc[r].x = fmaf(a[u][r].y, xv[u][1].x, acc[r].x);
+          acc[r].y = fmaf(a[u][r].y, xv[u][1].y, acc[r].y);
+          acc[r].x = fmaf(a[u][r].z, xv[u][2].x, acc[r].x);
+          acc[r].y = fmaf(a[u][r].z, xv[u][2].y, acc[r].y);
+          acc[r].x = fmaf(a[u][r].w, xv[u][3].x, acc[r].x);
+          acc[r].y = fmaf(a[u][r].w, xv[u][3].y, acc[r].y);
+        }
+    }
+    for (; b < b1; b += S) {
       const int J = m.blk_col[b];
       const float2* xr = x + (size_t)(4 * J) * W + c;
       float2 xv[4];

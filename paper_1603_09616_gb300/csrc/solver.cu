@@ -56,10 +56,80 @@ using namespace gb;
 // ------------------------------------------------------------ standalone SpMM
 namespace {
 
+// Single-column panels (FP32): one warp per block row, lane l takes the
+// stored blocks b0 + l, b0 + l + 32, ... with ALL W columns, so the warp reads
+// consecutive 64-byte blocks (one coalesced stream of the matrix) and each x
+// gather is one contiguous run of 4 rows x W columns; a xor-shuffle reduction
+// then sums the 4 x W complex partials.
+template <int WC>
+__device__ __forceinline__ void spmm_row_lanes_f(const gbk::DevMat& m, const float* __restrict__ A,
+                                                 const float2* __restrict__ x, float2* __restrict__ y, int lane,
+                                                 int I) {
+  float2 acc[4][WC];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < WC; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I] + lane; b < b1; b += 32) {
+    const int J = __ldg(m.blk_col + b);
+    const float4* ab = reinterpret_cast<const float4*>(A + (size_t)b * 16);
+    float4 a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = __ldg(ab + r);
+    float2 xv[4][WC];
+    const float2* xr = x + (size_t)(4 * J) * WC;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < WC; ++c) xv[t][c] = xr[t * WC + c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < WC; ++c) {
+        acc[r][c].x = fmaf(a[r].x, xv[0][c].x, acc[r][c].x);
+        acc[r][c].y = fmaf(a[r].x, xv[0][c].y, acc[r][c].y);
+        acc[r][c].x = fmaf(a[r].y, xv[1][c].x, acc[r][c].x);
+        acc[r][c].y = fmaf(a[r].y, xv[1][c].y, acc[r][c].y);
+        acc[r][c].x = fmaf(a[r].z, xv[2][c].x, acc[r][c].x);
+        acc[r][c].y = fmaf(a[r].z, xv[2][c].y, acc[r][c].y);
+        acc[r][c].x = fmaf(a[r].w, xv[3][c].x, acc[r][c].x);
+        acc[r][c].y = fmaf(a[r].w, xv[3][c].y, acc[r][c].y);
+      }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < WC; ++c) {
+        acc[r][c].x += __shfl_xor_sync(0xffffffffu, acc[r][c].x, off);
+        acc[r][c].y += __shfl_xor_sync(0xffffffffu, acc[r][c].y, off);
+      }
+  const int nrow = min(4, m.n - 4 * I);
+  // lane r * WC + c stores (row r, column c)
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < WC; ++c)
+      if (lane == r * WC + c && r < nrow) y[(size_t)(4 * I + r) * WC + c] = acc[r][c];
+}
+
 template <bool F64>
 __global__ void spmm_kernel(const gbk::DevMat m, int which, int W, const void* __restrict__ xv,
                             void* __restrict__ yv) {
   const int lane = threadIdx.x & 31;
+  if constexpr (!F64) {
+    if (W == 1) {  // measured: best for one column; W = 2 and 4 do better below
+      const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+      const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+      const float* A = which ? m.sb_hi : m.hb_hi;
+      const float2* x = static_cast<const float2*>(xv);
+      float2* y = static_cast<float2*>(yv);
+      for (long long I = warp0; I < m.nb; I += nwarps) spmm_row_lanes_f<1>(m, A, x, y, lane, (int)I);
+      return;
+    }
+  }
   if (W <= 8) {
     // narrow panels: one warp per block row, lanes split the stored blocks
     const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
