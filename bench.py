@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-spmm", action="store_true", help="skip the bundle-scale SpMM bandwidth measurement")
     ap.add_argument("--spmm-only", type=str, default="",
                     help="comma-separated panel widths: only the bundle SpMM bandwidth measurement")
+    ap.add_argument("--bundle", action="store_true",
+                    help="bundle-scale solve throughput, mixed versus plain FP64 (short runs)")
     ap.add_argument("--surrogate", action="store_true",
                     help="measure the learned surrogate with solver judge instead of the solver step")
     ap.add_argument("--maxit", type=int, default=0, help="override the workload's iteration cap")
@@ -467,6 +469,48 @@ def run_surrogate(args):
     print(json.dumps(res), flush=True)
 
 
+def run_bundle(args):
+    """Bundle-scale (N = 321,100) solve throughput: mixed versus plain FP64.
+
+    Both paths run the same short solve (maxit outer iterations, 64 shifts on
+    [-15, 10] eV + 0.02i) so that the outer-iteration rate is measured without
+    waiting for convergence: mixed on 256 random columns, FP64 on 16 (its
+    FP64-ALU-bound SpMMs take ~50x longer per column).  Reported: Krylov
+    iterations x columns per second for each, and their ratio per column.
+    """
+    import torch
+
+    import paper_1603_09616_gb300 as gbg
+    from synth import workload
+
+    torch.cuda.set_device(0)
+    wl = workload("bundle169")
+    mat = gbg.Matrix(wl["system"])
+    maxit = args.maxit or 20
+    out = {}
+    for prec, ncol in (("mixed", 256), ("fp64", 16)):
+        cols = wl["cols"][:ncol]
+        gbg.shifted_solve(mat, wl["z"], cols[:8], tol=1e-12, maxit=2, prec=prec, raise_on=(-1, -2, -3, -4))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = gbg.shifted_solve(mat, wl["z"], cols, tol=1e-12, maxit=maxit, prec=prec, w_rho=wl["w_rho"],
+                              w_edm=wl["w_edm"], raise_on=(-1, -2, -3, -4))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        it = r["iters"].cpu().numpy()
+        out[prec] = {"columns": ncol, "seconds": dt, "outer_iterations": int(it.max()),
+                     "column_iterations_per_s": float(it.sum()) / dt,
+                     "inner_per_outer": float(r["inner_iters"].cpu().numpy().sum() / max(it.sum(), 1))}
+    res = {"metric": "bundle-scale shifted-COCG column-iterations/s (mixed vs plain FP64)",
+           "value": out["mixed"]["column_iterations_per_s"], "unit": "column-iterations/s", "n_gpus": 1,
+           "higher_is_better": True, "mixed": out["mixed"], "fp64": out["fp64"],
+           "mixed_over_fp64": out["mixed"]["column_iterations_per_s"] / out["fp64"]["column_iterations_per_s"],
+           "config": {"workload": f"bundle169: N={wl['system'].n}, nnz={wl['system'].nnz}, 64 shifts on "
+                                  f"[-15,10] eV + 0.02i, {maxit} outer iterations (throughput, not convergence)"},
+           "data": "synthetic"}
+    print(json.dumps(res), flush=True)
+
+
 def run_profile_case(args):
     """One gb_shifted_solve of the workload (short with --maxit), for ncu."""
     import torch
@@ -498,6 +542,8 @@ if __name__ == "__main__":
         run_profile_case(a)
     elif a.surrogate:
         run_surrogate(a)
+    elif a.bundle:
+        run_bundle(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
