@@ -115,12 +115,94 @@ __device__ __forceinline__ void spmm_row_lanes_f(const gbk::DevMat& m, const flo
       if (lane == r * WC + c && r < nrow) y[(size_t)(4 * I + r) * WC + c] = acc[r][c];
 }
 
+// Narrow FP32 panels (W = 1, 2, 4): one warp per block row, lane l owns row
+// r = l % 4 of the stored blocks b0 + l / 4, b0 + l / 4 + 8, ...  The lanes of
+// a warp read 8 whole consecutive blocks per step (512 contiguous bytes: each
+// 32-byte sector requested once), the 4 lanes of a block share its x gather
+// (same addresses, one request), and every lane accumulates a single row, so
+// the reduction is three xor-shuffle levels over the 8 block slots.  Requires
+// x 16-byte aligned (float4 loads of the 4 x W gathered entries).
+// acc[c] += (row of a block) . x[4 rows, column c]; the complex x entry
+// (row t, column c) is float2 number t * WC + c of the gathered float4s.
+template <int WC>
+__device__ __forceinline__ void quad_fma(const float4& a, const float4 (&xv)[2 * WC], float2 (&acc)[WC]) {
+#pragma unroll
+  for (int c = 0; c < WC; ++c) {
+    float xr[4], xi[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int f = t * WC + c;
+      const float4 q = xv[f >> 1];
+      xr[t] = (f & 1) ? q.z : q.x;
+      xi[t] = (f & 1) ? q.w : q.y;
+    }
+    acc[c].x = fmaf(a.x, xr[0], fmaf(a.y, xr[1], fmaf(a.z, xr[2], fmaf(a.w, xr[3], acc[c].x))));
+    acc[c].y = fmaf(a.x, xi[0], fmaf(a.y, xi[1], fmaf(a.z, xi[2], fmaf(a.w, xi[3], acc[c].y))));
+  }
+}
+
+// Measured on the bundle Hamiltonian (N = 321,100): the kernel is bound by
+// loads in flight, so W = 1, 2 run two 8-block steps per lane at 32 registers
+// (64 warps per SM); W = 4 runs one step at 40 registers (48 warps), since at
+// 32 its spills cost more than the extra warps gain.
+template <int WC>
+__global__ void __launch_bounds__(256, WC == 4 ? 6 : 8)
+    spmm_quad_kernel(const gbk::DevMat m, const float* __restrict__ A, const float2* __restrict__ x,
+                     float2* __restrict__ y) {
+  const long long I = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (I >= m.nb) return;  // uniform per warp
+  const int lane = threadIdx.x & 31, r = lane & 3, s = lane >> 2;
+  constexpr int U = WC == 4 ? 1 : 2;  // steps of 8 blocks in flight per lane
+  constexpr int NQ = 2 * WC;  // float4 per gathered 4 x WC complex x block
+  float2 acc[WC];
+#pragma unroll
+  for (int c = 0; c < WC; ++c) acc[c] = make_float2(0.f, 0.f);
+  const int b1 = m.blk_ptr[I + 1];
+  const float4* __restrict__ A4 = reinterpret_cast<const float4*>(A);
+  const float4* __restrict__ X4 = reinterpret_cast<const float4*>(x);
+  int b = m.blk_ptr[I] + s;
+  for (; b + 8 * (U - 1) < b1; b += 8 * U) {
+    int J[U];
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) J[u] = __ldcs(m.blk_col + b + 8 * u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = __ldcs(A4 + (size_t)(b + 8 * u) * 4 + r);
+    float4 xv[U][NQ];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xv[u][q] = __ldg(X4 + (size_t)J[u] * NQ + q);
+#pragma unroll
+    for (int u = 0; u < U; ++u) quad_fma<WC>(a[u], xv[u], acc);
+  }
+  for (; b < b1; b += 8) {
+    const int J = __ldcs(m.blk_col + b);
+    const float4 a = __ldcs(A4 + (size_t)b * 4 + r);
+    float4 xv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) xv[q] = __ldg(X4 + (size_t)J * NQ + q);
+    quad_fma<WC>(a, xv, acc);
+  }
+#pragma unroll
+  for (int off = 4; off < 32; off <<= 1)
+#pragma unroll
+    for (int c = 0; c < WC; ++c) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
+    }
+  if (s == 0 && 4 * I + r < m.n) {
+#pragma unroll
+    for (int c = 0; c < WC; ++c) y[(size_t)(4 * I + r) * WC + c] = acc[c];
+  }
+}
+
 template <bool F64>
 __global__ void spmm_kernel(const gbk::DevMat m, int which, int W, const void* __restrict__ xv,
                             void* __restrict__ yv) {
   const int lane = threadIdx.x & 31;
   if constexpr (!F64) {
-    if (W == 1) {  // measured: best for one column; W = 2 and 4 do better below
+    if (W == 1) {  // x not 16-byte aligned (else spmm_quad_kernel): lane per block
       const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
       const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
       const float* A = which ? m.sb_hi : m.hb_hi;
@@ -359,10 +441,24 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
   const long long work = w <= 8 ? (long long)m->nb * 32 : (long long)m->nb * w;  // threads of work
   const int blocks = (int)std::min<long long>((work + threads - 1) / threads, (long long)nsm * 8);
-  if (prec == GB_FP64)
+  const bool quad = prec != GB_FP64 && (w == 1 || w == 2 || w == 4) &&
+                    (reinterpret_cast<uintptr_t>(xin) % 16) == 0;
+  if (quad) {
+    const float* A = which ? m->dm.sb_hi : m->dm.hb_hi;
+    const auto* xq = static_cast<const float2*>(xin);
+    auto* yq = static_cast<float2*>(y);
+    const unsigned qblocks = (unsigned)((m->nb + 7) / 8);  // 8 warps = 8 block rows per CTA
+    if (w == 1)
+      spmm_quad_kernel<1><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+    else if (w == 2)
+      spmm_quad_kernel<2><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+    else
+      spmm_quad_kernel<4><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+  } else if (prec == GB_FP64) {
     spmm_kernel<true><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
-  else
+  } else {
     spmm_kernel<false><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
+  }
   cudaError_t e = cudaGetLastError();
   if (pad) cudaFreeAsync(pad, s);
   if (e != cudaSuccess) return cuda_fail(e, "spmm launch");

@@ -396,9 +396,12 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float
 __device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ r,
                             float2* __restrict__ dA, float2* __restrict__ dB) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  // x = sum_k d_k is updated every other step with two directions (d_k from
+  // memory, d_{k+1} still in registers), so x is read and written half as
+  // often as r; the directions ping-pong between dA and dB.
   for (int k = 0; k < a.cheb_K; ++k) {
     const float Ak = a.cheb_A[k], Bk = a.cheb_B[k];
-    const bool last = k + 1 == a.cheb_K;
+    const bool last = k + 1 == a.cheb_K, even = !(k & 1);
     const float2* __restrict__ dk = (k & 1) ? dB : dA;
     float2* __restrict__ dn = (k & 1) ? dA : dB;
     for (int it = threadIdx.x; it < nb * W; it += TPB) {
@@ -411,17 +414,25 @@ __device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, flo
       for (int rr = 0; rr < 4; ++rr) {
         const size_t e = (size_t)(4 * I + rr) * W + c;
         dv[rr] = dk[e];
-        float2 xv = x[e];
-        xv.x += dv[rr].x;
-        xv.y += dv[rr].y;
-        x[e] = xv;
         float2 g = r[e];
         g.x -= acc[rr].x;
         g.y -= acc[rr].y;
         r[e] = g;
         rv[rr] = g;
       }
-      if (last) continue;
+      if (last) {  // d_K is not formed; d_{K-1} is still owed to x when K-1 is even
+        if (even) {
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const size_t e = (size_t)(4 * I + rr) * W + c;
+            float2 xv = x[e];
+            xv.x += dv[rr].x;
+            xv.y += dv[rr].y;
+            x[e] = xv;
+          }
+        }
+        continue;
+      }
       const float4* Mi = reinterpret_cast<const float4*>(a.m.minv32 + (size_t)I * 16);
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
@@ -432,7 +443,14 @@ __device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, flo
         float2 nd;
         nd.x = fmaf(Ak, dv[rr].x, Bk * zr.x);
         nd.y = fmaf(Ak, dv[rr].y, Bk * zr.y);
-        dn[(size_t)(4 * I + rr) * W + c] = nd;
+        const size_t e = (size_t)(4 * I + rr) * W + c;
+        dn[e] = nd;
+        if (even) {
+          float2 xv = x[e];
+          xv.x += dv[rr].x + nd.x;
+          xv.y += dv[rr].y + nd.y;
+          x[e] = xv;
+        }
       }
     }
     if (threadIdx.x == 0) ++sm.inner_count;

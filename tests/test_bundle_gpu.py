@@ -44,6 +44,11 @@ def test_bundle_spmm_full_size(bundle):
         assert rel(y, ref) < 1e-13
         y32 = mat.spmm(which, xt, prec="fp32").cpu().numpy()
         assert rel(y32, ref) < 5e-6
+    # narrow FP32 panels take the block-row-per-warp kernel
+    for w in (1, 2, 4):
+        x = rng.standard_normal((system.n, w)) + 1j * rng.standard_normal((system.n, w))
+        y32 = mat.spmm(0, torch.from_numpy(x).cuda(), prec="fp32").cpu().numpy()
+        assert rel(y32, system.h_csr() @ x) < 5e-6, w
 
 
 def test_small_bundle_solves_match_oracle():

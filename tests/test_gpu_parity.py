@@ -34,7 +34,7 @@ def dev():
 
 # ------------------------------------------------------------------ SpMM
 @pytest.mark.parametrize("system_fn", [lambda: chain_4orb(37, seed=2), lambda: ppv_chain(5, seed=4)])
-@pytest.mark.parametrize("w", [1, 3, 16, 64])
+@pytest.mark.parametrize("w", [1, 2, 3, 4, 16, 64])
 def test_spmm_fp64_and_fp32(dev, system_fn, w):
     system = system_fn()
     mat = gbg.Matrix(system)
@@ -47,6 +47,30 @@ def test_spmm_fp64_and_fp32(dev, system_fn, w):
         assert rel(y, A @ x) < 1e-14
         y32 = to_np(mat.spmm(which, xt, prec="fp32"))
         assert rel(y32, A @ x) < 2e-6
+    mat.close()
+
+
+@pytest.mark.parametrize("w", [1, 2, 4])
+def test_spmm_fp32_unaligned_x_matches_aligned(dev, w):
+    # x starting 8 bytes past a 16-byte boundary cannot take the float4-gather
+    # kernel of the narrow FP32 panels; both kernels must give the product
+    # (n % 4 == 0 here, so x is read in place, not through a padded copy)
+    system = chain_4orb(37, seed=2)
+    assert system.n % 4 == 0
+    mat = gbg.Matrix(system)
+    H, _ = system.dense()
+    rng = np.random.default_rng(10 + w)
+    x = rng.standard_normal((system.n, w)) + 1j * rng.standard_normal((system.n, w))
+    buf = torch.zeros(system.n * w + 1, dtype=torch.complex64, device=dev)
+    xa = buf[: system.n * w].view(system.n, w)
+    xu = buf[1 : system.n * w + 1].view(system.n, w)
+    assert xa.data_ptr() % 16 == 0 and xu.data_ptr() % 16 == 8
+    xa.copy_(torch.from_numpy(x))
+    ya = to_np(mat.spmm(0, xa, prec="fp32"))
+    xu.copy_(torch.from_numpy(x))
+    yu = to_np(mat.spmm(0, xu, prec="fp32"))
+    assert rel(ya, H @ x) < 2e-6
+    assert rel(yu, H @ x) < 2e-6
     mat.close()
 
 
