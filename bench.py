@@ -28,15 +28,16 @@ UNIT = "RHS·shift solves/s"
 FP32_LANES_PER_SM = 128
 NOMINAL_MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) from ncu captures of the current kernels, used to
-# fill roofline.traffic (profiles/team_kernel_mixed_ppv1900.md and
-# profiles/spmm_kernel_bundle169.md give the commands):
-#  team_kernel<mixed>, ppv1900 with 60 outer iterations on all 1900 columns:
-#    200.79 GB / 114,000 column-iterations; scaled to a launch by its
-#    column-iterations (history writes, panel vectors and the final replay
-#    all grow with the iteration count).
-#  spmm_kernel, FP32, one column, bundle169 H: 337.09 MB per launch.
-TEAM_MIXED_DRAM_BYTES_PER_COL_ITER = 200.792769e9 / (60 * 1900)
-SPMM_F32_W1_DRAM_BYTES = 337.093376e6
+# fill roofline.traffic (None: not captured since the kernel last changed;
+# the commands are in profiles/team_kernel_mixed_ppv1900.md and
+# profiles/spmm_kernel_bundle169.md).
+#  team_kernel<mixed>, ppv1900, 60 outer iterations on all 1900 columns:
+#    bytes per column-iteration, scaled to a launch by its column-iterations
+#    (history writes, panel vectors and the final replay all grow with the
+#    iteration count).
+#  spmm_kernel, FP32, one column, bundle169 H: bytes per launch.
+TEAM_MIXED_DRAM_BYTES_PER_COL_ITER = 173.621605e9 / (60 * 1900)
+SPMM_F32_W1_DRAM_BYTES = 333.958912e6
 
 
 def parse():
@@ -259,7 +260,8 @@ def run_ours(args):
             "unit": "TFLOP/s",
             "frac": achieved_tf / peak_tf,
             "traffic": TEAM_MIXED_DRAM_BYTES_PER_COL_ITER * float(iters.sum())
-            if (wl["prec"] == "mixed" and W == 8 and args.workload == "ppv1900") else None,
+            if (TEAM_MIXED_DRAM_BYTES_PER_COL_ITER and wl["prec"] == "mixed" and W == 8
+                and args.workload == "ppv1900") else None,
             "traffic_note": "ncu dram bytes of a 60-iteration capture, scaled by column-iterations",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max)",
             "achieved_model": flops_note,
