@@ -82,6 +82,19 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the initialised process group (x itself
+    without one): replicas are timed by the slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -205,11 +218,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), "cuda")
     ms_per_step = total_ms / args.steps
     solves = K * nrhs
     value = world * solves * args.steps / (total_ms / 1e3)

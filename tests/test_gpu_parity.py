@@ -75,11 +75,11 @@ def test_spmm_fp32_unaligned_x_matches_aligned(dev, w):
 
 
 # ------------------------------------------------------------------ shifted solve
-def run_case(dev, system, z, cols, prec, tol, maxit, panel=0, want_g=True, seed_shift=-1):
+def run_case(dev, system, z, cols, prec, tol, maxit, panel=0, want_g=True, seed_shift=-1, flags=0):
     w_rho, w_edm = fermi_weights(z)
     mat = gbg.Matrix(system)
     out = gbg.shifted_solve(mat, z, cols, tol=tol, maxit=maxit, prec=prec, w_rho=w_rho, w_edm=w_edm,
-                            panel=panel, want_g=want_g, seed_shift=seed_shift)
+                            panel=panel, want_g=want_g, seed_shift=seed_shift, flags=flags)
     torch.cuda.synchronize()
     ref = oracle.solve_outputs(system, z, cols, w_rho, w_edm)
     mat.close()
@@ -140,6 +140,22 @@ def test_mixed_small(dev):
     z = shift_grid(-10, 6, 48, 0.05)
     cols = np.arange(0, system.n, 7, dtype=np.int32)
     out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=8)
+    check_outputs(out, ref, 1e-6)
+
+
+@pytest.mark.parametrize("flags", [0, 2, 4, 6])
+def test_mixed_inner_method_and_placement(dev, flags):
+    # bit 2: CG instead of Chebyshev on the FP32 inner levels; bit 1: inner
+    # vectors in shared memory (they fit at this size).  Every combination
+    # must reach the oracle; the plan reports the placement.
+    system = ppv_chain(4, seed=9)  # N = 152
+    z = shift_grid(-10, 6, 40, 0.05)
+    cols = np.arange(1, system.n, 9, dtype=np.int32)  # 17 columns: ragged last panel
+    mat = gbg.Matrix(system)
+    plan = gbg.solve_plan(mat, z, cols, prec="mixed", panel=4, flags=flags)
+    mat.close()
+    assert plan["cg_smem"] == bool(flags & 2)
+    out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=4, flags=flags)
     check_outputs(out, ref, 1e-6)
 
 
