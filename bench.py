@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-spmm", action="store_true", help="skip the bundle-scale SpMM bandwidth measurement")
     ap.add_argument("--spmm-only", type=str, default="",
                     help="comma-separated panel widths: only the bundle SpMM bandwidth measurement")
+    ap.add_argument("--batched", action="store_true",
+                    help="uneven-chain batch (512 chains, sampled RHS) in one persistent launch")
     ap.add_argument("--bundle", action="store_true",
                     help="bundle-scale solve throughput, mixed versus plain FP64 (short runs)")
     ap.add_argument("--surrogate", action="store_true",
@@ -538,6 +540,50 @@ def run_bundle(args):
     print(json.dumps(res), flush=True)
 
 
+def run_batched(args):
+    """Uneven-chain batch: 512 chains (76..1900 orbitals, 32..256 shifts each,
+    eta 0.05, tol 1e-6, mixed), two sampled unit right-hand sides per chain,
+    in one gb_shifted_solve_batched launch (2-column panels).  Solves/s =
+    sum over chains of shifts x right-hand sides / launch time (CUDA events)."""
+    import torch
+
+    import paper_1603_09616_gb300 as gbg
+    from synth import uneven_batch
+
+    torch.cuda.set_device(0)
+    systems, problems = uneven_batch(eta=0.05)
+    mats = [gbg.Matrix(s) for s in systems]
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        res, info = gbg.shifted_solve_batched(mats, problems, prec="mixed", panel=2)
+        assert info["status"] == 0, info["message"]
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, info = gbg.shifted_solve_batched(mats, problems, prec="mixed", panel=2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    pairs = sum(len(p["z"]) * len(p["cols"]) for p in problems)
+    iters = np.concatenate([r["iters"].cpu().numpy() for r in res])
+    n = np.array([s.n for s in systems])
+    print(json.dumps({
+        "metric": "uneven-chain batch RHS·shift solves/s (one persistent launch)", "value": pairs / (ms / 1e3),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32x2+f32 (f64 scalars)", "data": "synthetic",
+        "config": {"workload": f"512 PPV-like chains, N {n.min()}..{n.max()} (mean {n.mean():.0f}), "
+                               f"32..256 shifts each on [-15,10] eV + 0.05i, 2 sampled RHS per chain, tol 1e-6",
+                   "pairs": int(pairs), "panel": 2},
+        "krylov_iters_per_s": float(iters.sum()) / (ms / 1e3),
+        "outer_iters": {"min": int(iters.min()), "median": int(np.median(iters)), "max": int(iters.max())},
+    }), flush=True)
+    for m in mats:
+        m.close()
+
+
 def run_profile_case(args):
     """One gb_shifted_solve of the workload (short with --maxit), for ncu."""
     import torch
@@ -571,6 +617,8 @@ if __name__ == "__main__":
         run_surrogate(a)
     elif a.bundle:
         run_bundle(a)
+    elif a.batched:
+        run_batched(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -17,6 +17,7 @@ from .tb import (  # noqa: F401
     ppv_chain,
     ppv_bundle,
     uneven_chains,
+    uneven_batch,
     shift_grid,
     fermi_weights,
     random_columns,

@@ -264,6 +264,27 @@ def uneven_chains(n_chains: int = 512, seed: int = 2, mono_range=(2, 50), shift_
     return out
 
 
+def uneven_batch(n_chains: int = 512, cols_per_chain: int = 2, seed: int = 2, eta: float = 0.02,
+                 tol: float = 1e-6, maxit: int = 16000):
+    """The uneven-chain batch with sampled right-hand sides per chain.
+
+    Chains as in ``uneven_chains`` (2..50 monomers, 32..256 shifts each on
+    [-15, 10] eV + i*eta); each chain gets ``cols_per_chain`` distinct random
+    unit right-hand sides (always including its first orbital), Fermi weights
+    and the common tolerance / iteration cap.  Returns (systems, problems).
+    """
+    rng = np.random.default_rng(seed + 7919)
+    systems, problems = [], []
+    for sysm, k in uneven_chains(n_chains, seed=seed):
+        z = shift_grid(-15.0, 10.0, k, eta)
+        w_rho, w_edm = fermi_weights(z)
+        extra = rng.choice(np.arange(1, sysm.n), size=cols_per_chain - 1, replace=False)
+        cols = np.sort(np.concatenate([[0], extra])).astype(np.int32)
+        systems.append(sysm)
+        problems.append(dict(z=z, cols=cols, w_rho=w_rho, w_edm=w_edm, tol=tol, maxit=maxit))
+    return systems, problems
+
+
 def shift_grid(e_min: float, e_max: float, n_shift: int, eta: float) -> np.ndarray:
     """Energy shifts z_k = eps_k + i*eta, eps_k evenly spaced on [e_min, e_max]."""
     return np.linspace(e_min, e_max, n_shift) + 1j * eta
