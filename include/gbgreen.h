@@ -201,6 +201,30 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gb_correct_unconverged — correction solve for the columns of a finished
+ * gb_shifted_solve whose shifts missed tol (col_status bit 4; columns with a
+ * breakdown or an indefinite S are left alone).  The paper's equation is the
+ * same (Introduction); the correction is this library's answer to shifted
+ * COCG's limited attainable accuracy: each such column is solved again alone,
+ * in plain FP64, with its worst unconverged shift (largest resid) as the seed,
+ * and its ldos, rho, edm, q, e_loc, iters, inner_iters, converged, resid,
+ * g_proj and col_status entries in `out` are overwritten.
+ *
+ * `p` and `out` are those of the first solve (out->col_status and out->resid
+ * are required).  `workspace`: caller-owned device memory of at least
+ * gb_correct_workspace_size(m, p, out->g_proj != NULL) bytes, 256-byte
+ * aligned (one single-column solve plus its temporary outputs).  Synchronous.
+ * `ncorrected` (host, may be NULL) receives the number of columns that now
+ * meet tol.  Returns GB_OK when every re-solved column meets tol, GB_ENOCONV
+ * if some still miss it (their outputs are then the FP64 solve's).
+ */
+gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
+                                 void* workspace, size_t workspace_bytes, void* stream, int32_t* ncorrected);
+
+/* Bytes of workspace gb_correct_unconverged needs (0: invalid parameters). */
+size_t gb_correct_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t want_g);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
  * Each system s solves (z_k S_s - H_s) x = e_j for its own shifts and columns

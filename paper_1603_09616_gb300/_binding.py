@@ -110,6 +110,11 @@ def load() -> C.CDLL:
     lib.gb_shifted_solve.restype = C.c_int
     lib.gb_shifted_solve.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p,
                                      C.c_size_t, C.c_void_p]
+    lib.gb_correct_unconverged.restype = C.c_int
+    lib.gb_correct_unconverged.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p,
+                                           C.c_size_t, C.c_void_p, C.POINTER(C.c_int32)]
+    lib.gb_correct_workspace_size.restype = C.c_size_t
+    lib.gb_correct_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
     lib.gb_shifted_solve_static.restype = C.c_int
     lib.gb_shifted_solve_static.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p]
     lib.gb_static_scratch_bytes.restype = C.c_size_t
@@ -271,12 +276,15 @@ def solve_plan(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", panel=0
 
 def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
                   inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, workspace=None, stream=None, flags=0,
-                  raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD)):
+                  raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD), correct=False):
     """Solve (z_k S - H) x = e_j for all shifts and columns; returns device tensors.
 
     Keys: ldos [K, nrhs], rho / edm [P], q / e_loc [nrhs], iters [nrhs],
     converged [K, nrhs] (uint8), resid [K, nrhs], g_proj [K, P] complex (if
-    want_g), off [nrhs+1] (host, packed offsets), status (int).
+    want_g), off [nrhs+1] (host, packed offsets), status (int).  With
+    ``correct=True`` a GB_ENOCONV result is passed to gb_correct_unconverged
+    (FP64 re-solve of the failing columns with a switched seed); ``corrected``
+    then holds the number of columns it fixed.
     """
     import torch
 
@@ -318,6 +326,19 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
     res["message"] = lib.gb_last_error().decode()
     res["off"] = off
     res["workspace"] = workspace
+    if correct and st == GB_ENOCONV:
+        cneed = lib.gb_correct_workspace_size(mat.handle, C.byref(p), int(want_g))
+        if cneed == 0:
+            raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+        cws = workspace if workspace.numel() >= cneed else torch.empty(int(cneed), dtype=torch.uint8, device=dev)
+        fixed = C.c_int32(0)
+        st = lib.gb_correct_unconverged(mat.handle, C.byref(p), C.byref(o), C.c_void_p(cws.data_ptr()),
+                                        C.c_size_t(cws.numel()), _stream_handle(stream), C.byref(fixed))
+        if st in raise_on:
+            _check(st)
+        res["status"] = st
+        res["message"] = lib.gb_last_error().decode()
+        res["corrected"] = int(fixed.value)
     return res
 
 
@@ -390,14 +411,16 @@ def _alloc_outputs(mat, K, cols, w_rho, w_edm, want_g, dev):
 
 
 def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, workspace=None, stream=None,
-                          tune_probe_maxit=0):
+                          tune_probe_maxit=0, correct=False):
     """Solve many independent systems in one persistent launch.
 
     ``problems`` is a list of dicts with keys z, cols, tol, maxit and optional
     w_rho, w_edm (one per matrix in ``mats``).  With ``tune_probe_maxit > 0``
     the panel width is first picked by the library's autotuner
-    (gb_tune_panel_batched) on probe runs of that many iterations.  Returns a
-    list of per-system result dicts plus the batch status/message/panel.
+    (gb_tune_panel_batched) on probe runs of that many iterations.  With
+    ``correct=True`` a GB_ENOCONV batch is passed system by system to
+    gb_correct_unconverged.  Returns a list of per-system result dicts plus the
+    batch status/message/panel (and ``corrected`` columns).
     """
     import torch
 
@@ -441,5 +464,27 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
                                       C.c_size_t(workspace.numel()), _stream_handle(stream))
     if st in (GB_EINVAL, GB_ENOMEM, GB_ECUDA):
         _check(st)
-    info.update(status=st, message=lib.gb_last_error().decode(), panel=panel, workspace=workspace)
+    msg = lib.gb_last_error().decode()
+    if correct and st == GB_ENOCONV:
+        fixed_total, left = 0, 0
+        for s_, mat in enumerate(mats):
+            cneed = lib.gb_correct_workspace_size(mat.handle, C.byref(params[s_]), int(want_g))
+            if cneed == 0:
+                raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+            if workspace.numel() < cneed:
+                workspace = torch.empty(int(cneed), dtype=torch.uint8, device=dev)
+            fixed = C.c_int32(0)
+            r = lib.gb_correct_unconverged(mat.handle, C.byref(params[s_]), C.byref(outs[s_]),
+                                           C.c_void_p(workspace.data_ptr()), C.c_size_t(workspace.numel()),
+                                           _stream_handle(stream), C.byref(fixed))
+            if r in (GB_EINVAL, GB_ENOMEM, GB_ECUDA):
+                _check(r)
+            fixed_total += int(fixed.value)
+            if r != GB_OK:
+                left += 1
+                msg = f"system {s_}: " + lib.gb_last_error().decode()
+        st = GB_OK if left == 0 else GB_ENOCONV
+        msg = "" if left == 0 else msg
+        info["corrected"] = fixed_total
+    info.update(status=st, message=msg, panel=panel, workspace=workspace)
     return results, info

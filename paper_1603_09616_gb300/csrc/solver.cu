@@ -757,6 +757,187 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
 
 }  // extern "C"
 
+// ------------------------------------------------------------ correction solve
+// Shifted COCG with one seed can stagnate for a shift whose shifted residual
+// loses attainable accuracy (observed near the gap of some PPV-like chains at
+// eta = 0.02, in the mixed path and once in FP64).  The correction re-solves
+// each such column alone in plain FP64 with its worst unconverged shift as the
+// seed, so that shift's residual is the seed's own, and copies the column's
+// results over the first solve's.
+namespace {
+
+struct CorrLayout {
+  size_t plan_total, o_ldos, o_rho, o_edm, o_q, o_e, o_it, o_conv, o_res, o_g, o_in, o_st, total;
+};
+
+// Workspace of one single-column FP64 correction solve (its plan depends on
+// maxit, the shift count and the longest pattern row, not on the column)
+// followed by that column's temporary outputs.
+gb_status corr_layout(const gb_matrix* m, const gb_solve_params* p, bool want_g, CorrLayout* L) {
+  if (!p->rhs_cols || p->nrhs < 1) return fail(GB_EINVAL, "rhs_cols must hold nrhs >= 1 columns");
+  gb_solve_params q = *p;
+  const int32_t col0 = p->rhs_cols[0];
+  q.nrhs = 1;
+  q.rhs_cols = &col0;
+  q.prec = GB_FP64;
+  q.seed_shift = -1;
+  q.panel = 1;
+  q.flags = 0;
+  q.inner_tol = 0.0;
+  Plan pl;
+  const gb_status st = make_plan(m, &q, want_g, &pl);
+  if (st != GB_OK) return st;
+  const size_t K = p->nshift, mr = (size_t)std::max(m->max_row, 1);
+  size_t off = align256(pl.total);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L->plan_total = pl.total;
+  L->o_ldos = take(K * 8);
+  L->o_rho = take(mr * 8);
+  L->o_edm = take(mr * 8);
+  L->o_q = take(8);
+  L->o_e = take(8);
+  L->o_it = take(4);
+  L->o_conv = take(K);
+  L->o_res = take(K * 8);
+  L->o_g = want_g ? take(K * mr * 16) : 0;
+  L->o_in = take(4);
+  L->o_st = take(4);
+  L->total = off + 256;
+  return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_correct_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t want_g) {
+  clear_error();
+  if (!m || !p) {
+    fail(GB_EINVAL, "NULL argument");
+    return 0;
+  }
+  CorrLayout L;
+  if (corr_layout(m, p, want_g != 0, &L) != GB_OK) return 0;
+  return L.total;
+}
+
+gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
+                                 void* workspace, size_t workspace_bytes, void* stream, int32_t* ncorrected) {
+  clear_error();
+  if (ncorrected) *ncorrected = 0;
+  if (!m || !p || !out) return fail(GB_EINVAL, "NULL argument");
+  if (!out->col_status || !out->resid) return fail(GB_EINVAL, "col_status and resid of the first solve are required");
+  {
+    Plan full;  // validates every parameter of the first solve
+    const gb_status st = make_plan(m, p, out->g_proj != nullptr, &full);
+    if (st != GB_OK) return st;
+  }
+  const bool want_g = out->g_proj != nullptr;
+  CorrLayout L;
+  gb_status st = corr_layout(m, p, want_g, &L);
+  if (st != GB_OK) return st;
+  if (!workspace) return fail(GB_EINVAL, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(GB_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total)
+    return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int K = p->nshift, nrhs = p->nrhs;
+  std::vector<int32_t> hst(nrhs);
+  std::vector<double> hres((size_t)K * nrhs);
+  std::vector<uint8_t> hconv(out->converged ? (size_t)K * nrhs : 0);
+  GB_CUDA(cudaMemcpyAsync(hst.data(), out->col_status, sizeof(int32_t) * nrhs, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaMemcpyAsync(hres.data(), out->resid, sizeof(double) * K * nrhs, cudaMemcpyDeviceToHost, s));
+  if (out->converged)
+    GB_CUDA(cudaMemcpyAsync(hconv.data(), out->converged, (size_t)K * nrhs, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  const std::vector<int64_t>& rp = m->h_row_ptr;
+  std::vector<long long> off(nrhs + 1, 0);
+  for (int c = 0; c < nrhs; ++c) {
+    const int j = p->rhs_cols[c];
+    off[c + 1] = off[c] + (rp[j + 1] - rp[j]);
+  }
+  const long long P = off[nrhs];
+  char* wsb = static_cast<char*>(workspace);
+  int fixed = 0, left = 0;
+  for (int c = 0; c < nrhs; ++c) {
+    const int sc = hst[c];
+    if (!(sc & gbk::kStNoConv) || (sc & (gbk::kStBreakdown | gbk::kStNotSPD))) continue;
+    int kw = -1;  // the column's worst unconverged shift becomes the seed
+    double rw = -1.0;
+    for (int k = 0; k < K; ++k) {
+      const size_t e = (size_t)k * nrhs + c;
+      const bool conv = out->converged ? hconv[e] != 0 : hres[e] <= p->tol;
+      if (!conv && hres[e] > rw) {
+        rw = hres[e];
+        kw = k;
+      }
+    }
+    if (kw < 0) kw = K / 2;
+    gb_solve_params q = *p;
+    const int32_t col = p->rhs_cols[c];
+    q.nrhs = 1;
+    q.rhs_cols = &col;
+    q.prec = GB_FP64;
+    q.seed_shift = kw;
+    q.panel = 1;
+    q.flags = 0;
+    q.inner_tol = 0.0;
+    gb_outputs t{};
+    t.ldos = out->ldos ? reinterpret_cast<double*>(wsb + L.o_ldos) : nullptr;
+    t.rho = out->rho ? reinterpret_cast<double*>(wsb + L.o_rho) : nullptr;
+    t.edm = out->edm ? reinterpret_cast<double*>(wsb + L.o_edm) : nullptr;
+    t.q = out->q ? reinterpret_cast<double*>(wsb + L.o_q) : nullptr;
+    t.e_loc = out->e_loc ? reinterpret_cast<double*>(wsb + L.o_e) : nullptr;
+    t.iters = out->iters ? reinterpret_cast<int32_t*>(wsb + L.o_it) : nullptr;
+    t.converged = out->converged ? reinterpret_cast<uint8_t*>(wsb + L.o_conv) : nullptr;
+    t.resid = reinterpret_cast<double*>(wsb + L.o_res);
+    t.g_proj = want_g ? reinterpret_cast<double*>(wsb + L.o_g) : nullptr;
+    t.inner_iters = out->inner_iters ? reinterpret_cast<int32_t*>(wsb + L.o_in) : nullptr;
+    t.col_status = reinterpret_cast<int32_t*>(wsb + L.o_st);
+    const gb_status sub = gb_shifted_solve(m, &q, &t, workspace, L.plan_total, stream);
+    if (sub != GB_OK && sub != GB_ENOCONV) return sub;
+    // copy column c of the single-column results into the first solve's outputs
+    const long long mc = off[c + 1] - off[c];
+    auto column = [&](void* dst, const void* src, size_t esz) {  // [K][nrhs] column c <- [K][1]
+      return cudaMemcpy2DAsync(static_cast<char*>(dst) + esz * c, esz * nrhs, src, esz, esz, K,
+                               cudaMemcpyDeviceToDevice, s);
+    };
+    auto one = [&](void* dst, const void* src, size_t esz) {
+      return cudaMemcpyAsync(static_cast<char*>(dst) + esz * c, src, esz, cudaMemcpyDeviceToDevice, s);
+    };
+    if (out->ldos) GB_CUDA(column(out->ldos, t.ldos, sizeof(double)));
+    if (out->converged) GB_CUDA(column(out->converged, t.converged, 1));
+    GB_CUDA(column(out->resid, t.resid, sizeof(double)));
+    if (out->rho) GB_CUDA(cudaMemcpyAsync(out->rho + off[c], t.rho, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
+    if (out->edm) GB_CUDA(cudaMemcpyAsync(out->edm + off[c], t.edm, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
+    if (out->q) GB_CUDA(one(out->q, t.q, sizeof(double)));
+    if (out->e_loc) GB_CUDA(one(out->e_loc, t.e_loc, sizeof(double)));
+    if (out->iters) GB_CUDA(one(out->iters, t.iters, sizeof(int32_t)));
+    if (out->inner_iters) GB_CUDA(one(out->inner_iters, t.inner_iters, sizeof(int32_t)));
+    GB_CUDA(one(out->col_status, t.col_status, sizeof(int32_t)));
+    if (want_g)
+      GB_CUDA(cudaMemcpy2DAsync(out->g_proj + 2 * off[c], 16 * (size_t)P, t.g_proj, 16 * (size_t)mc, 16 * (size_t)mc,
+                                K, cudaMemcpyDeviceToDevice, s));
+    // the next column's solve reuses the temporaries: gb_shifted_solve is
+    // stream-ordered after these copies
+    if (sub == GB_OK)
+      ++fixed;
+    else
+      ++left;
+  }
+  GB_CUDA(cudaStreamSynchronize(s));
+  if (ncorrected) *ncorrected = fixed;
+  if (left > 0)
+    return fail(GB_ENOCONV, "%d column(s) still miss tol after the FP64 correction solve", left);
+  return GB_OK;
+}
+
+}  // extern "C"
+
 // ------------------------------------------------------------ allocation-free solve
 // gb_shifted_solve_static: the same solve for callers that may not allocate
 // memory once they are running — e.g. an application whose device memory is

@@ -104,3 +104,27 @@ def test_batched_512_uneven_chains_sampled_columns():
             assert rel(res[i][key].cpu().numpy(), ref[key]) < 1e-6, (int(i), key)
     for m in mats:
         m.close()
+
+
+def test_batched_correction_solve():
+    # Two chains of the uneven batch at eta 0.02 whose mixed solve stagnates on
+    # one column each (331: N = 228, 115 shifts; 69: N = 570, 183 shifts), in
+    # one launch; the per-system correction must bring every pair to tol.
+    torch.cuda.set_device(0)
+    systems, problems = uneven_batch(eta=0.02)
+    pick = [331, 69]
+    systems = [systems[i] for i in pick]
+    problems = [problems[i] for i in pick]
+    mats = [gbg.Matrix(s) for s in systems]
+    res, info = gbg.shifted_solve_batched(mats, problems, prec="mixed", panel=2)
+    assert info["status"] == gbg._binding.GB_ENOCONV
+    res, info = gbg.shifted_solve_batched(mats, problems, prec="mixed", panel=2, correct=True)
+    assert info["status"] == 0, info["message"]
+    assert info["corrected"] >= 2
+    for sysm, pr, out in zip(systems, problems, res):
+        assert out["converged"].cpu().numpy().all()
+        ref = oracle.solve_outputs(sysm, pr["z"], pr["cols"], pr["w_rho"], pr["w_edm"])
+        for key in ("ldos", "rho", "edm", "q", "e_loc"):
+            assert rel(out[key].cpu().numpy(), ref[key]) < 1e-6, key
+    for m in mats:
+        m.close()

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import chain_4orb, fermi_weights, ppv_chain, shift_grid
+from synth import chain_4orb, fermi_weights, ppv_chain, shift_grid, uneven_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -203,3 +203,25 @@ def test_indefinite_overlap_reported(dev):
                             raise_on=())
     assert out["status"] == gbg._binding.GB_ENOTSPD
     mat.close()
+
+
+def test_correction_solve_fixes_stagnating_column(dev):
+    # Chain 331 of the uneven batch at eta 0.02 (N = 228, 115 shifts): the mixed
+    # path's residual for one column stagnates near a gap shift above tol 1e-6.
+    # gb_correct_unconverged re-solves that column in FP64 with the stalled
+    # shift as the seed; every pair must then meet tol and match the oracle.
+    systems, problems = uneven_batch(eta=0.02)
+    sysm, pr = systems[331], problems[331]
+    assert sysm.n == 228 and len(pr["z"]) == 115
+    mat = gbg.Matrix(sysm)
+    kw = dict(tol=1e-6, maxit=16000, prec="mixed", w_rho=pr["w_rho"], w_edm=pr["w_edm"], panel=2, want_g=True)
+    first = gbg.shifted_solve(mat, pr["z"], pr["cols"], **kw)
+    assert first["status"] == gbg._binding.GB_ENOCONV
+    out = gbg.shifted_solve(mat, pr["z"], pr["cols"], correct=True, **kw)
+    mat.close()
+    assert out["status"] == 0, out["message"]
+    assert out["corrected"] >= 1
+    assert to_np(out["converged"]).all()
+    assert (to_np(out["resid"]) <= 1e-6).all()
+    ref = oracle.solve_outputs(sysm, pr["z"], pr["cols"], pr["w_rho"], pr["w_edm"])
+    check_outputs(out, ref, 1e-6)
