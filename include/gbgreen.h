@@ -148,7 +148,11 @@ typedef struct {
   int32_t flags;         /* bit 1: keep the inner-CG vectors of a panel in shared
                             memory when they fit (fewer teams per SM);
                             bit 2: mixed path uses CG instead of the Chebyshev
-                            inner iteration for its FP32 levels              */
+                            inner iteration for its FP32 levels;
+                            bit 3: mixed path solves its FP32 levels with the
+                            banded Cholesky factor of S (two triangular solves,
+                            no iteration) when S's half-bandwidth is <= 63;
+                            otherwise the bit is ignored                     */
   int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
   int32_t reserved;
 } gb_solve_params;

@@ -265,4 +265,62 @@ void preconditioned_s_bounds(HostBSR* hb) {
   hb->lam_max = bisect(m - 1);
 }
 
+// Banded Cholesky of S for an exact S^-1 in the mixed path (triangular solves
+// instead of an iteration).  S's entries come from the 4x4 blocks; rows past n
+// (block padding) are identity.  Plain column-by-column factorisation inside the
+// band, FP64, then rounded to FP32 for the device; skipped (chol_bw = 0) when the
+// half-bandwidth exceeds 63 or a pivot is not positive.
+void band_cholesky(HostBSR* hb) {
+  hb->chol_bw = 0;
+  const int64_t n4 = 4 * hb->nb, n = hb->n;
+  int64_t bw = 0;
+  for (int64_t I = 0; I < hb->nb; ++I)
+    for (int32_t b = hb->blk_ptr[I]; b < hb->blk_ptr[I + 1]; ++b) {
+      const int64_t J = hb->blk_col[b];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+          const int64_t i = 4 * I + r, j = 4 * J + c;
+          if (i < n && j < n && j <= i && hb->blk_s[(size_t)b * 16 + r * 4 + c] != 0.0) bw = std::max(bw, i - j);
+        }
+    }
+  if (bw > 63) return;
+  const int64_t w = bw + 1;  // stored band entries per row, diagonal last
+  std::vector<double> L((size_t)(n4 * w), 0.0);
+  auto at = [&](int64_t i, int64_t j) -> double& { return L[(size_t)(i * w + (j - i + bw))]; };
+  for (int64_t I = 0; I < hb->nb; ++I)
+    for (int32_t b = hb->blk_ptr[I]; b < hb->blk_ptr[I + 1]; ++b) {
+      const int64_t J = hb->blk_col[b];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+          const int64_t i = 4 * I + r, j = 4 * J + c;
+          if (i < n && j < n && j <= i && i - j <= bw) at(i, j) = hb->blk_s[(size_t)b * 16 + r * 4 + c];
+        }
+    }
+  for (int64_t i = n; i < n4; ++i) at(i, i) = 1.0;
+  for (int64_t i = 0; i < n4; ++i) {
+    const int64_t j0 = std::max<int64_t>(0, i - bw);
+    for (int64_t j = j0; j <= i; ++j) {
+      double sum = at(i, j);
+      for (int64_t k = std::max(j0, j - bw); k < j; ++k) sum -= at(i, k) * at(j, k);
+      if (j < i) {
+        at(i, j) = sum / at(j, j);
+      } else {
+        if (!(sum > 0.0)) return;
+        at(i, i) = std::sqrt(sum);
+      }
+    }
+  }
+  hb->chol_up.assign((size_t)n4 * 64, 0.f);
+  hb->chol_row.assign((size_t)n4 * 64, 0.f);
+  hb->chol_invd.assign((size_t)n4, 0.f);
+  for (int64_t i = 0; i < n4; ++i) {
+    hb->chol_invd[i] = (float)(1.0 / at(i, i));
+    for (int64_t t = 0; t < bw; ++t) {
+      if (i + 1 + t < n4) hb->chol_up[(size_t)i * 64 + t] = (float)at(i + 1 + t, i);
+      if (i - 1 - t >= 0) hb->chol_row[(size_t)i * 64 + t] = (float)at(i, i - 1 - t);
+    }
+  }
+  hb->chol_bw = (int32_t)bw;
+}
+
 }  // namespace gb

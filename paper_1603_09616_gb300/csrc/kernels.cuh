@@ -55,6 +55,10 @@ struct DevMat {
   const double* h_val;
   const double* s_val;
   double s_lam_min, s_lam_max;  // spectrum bounds of the block-Jacobi-preconditioned S
+  int chol_bw;  // half-bandwidth of the banded Cholesky factor of S (0: none)
+  const float* chol_up;    // [4 nb][64] L(i+1+t, i)
+  const float* chol_row;   // [4 nb][64] L(i, i-1-t)
+  const float* chol_invd;  // [4 nb] 1 / L(i, i)
 };
 
 // ------------------------------------------------------------ complex FP64

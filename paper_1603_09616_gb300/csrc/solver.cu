@@ -297,6 +297,7 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
   if (st != GB_OK) return st;
   preconditioned_s_bounds(&hb);
+  band_cholesky(&hb);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
   GB_CUDA(cudaGetDevice(&dev));
@@ -316,6 +317,9 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   const size_t o_mi = take(sizeof(double) * nbl * 16), o_m32 = take(sizeof(float) * nbl * 16);
   const size_t o_rp = take(sizeof(int) * (n + 1)), o_ci = take(sizeof(int) * nnz);
   const size_t o_hv = take(sizeof(double) * nnz), o_sv = take(sizeof(double) * nnz);
+  const size_t nch = hb.chol_bw > 0 ? 4 * nbl : 0;
+  const size_t o_cu = take(sizeof(float) * nch * 64), o_cr = take(sizeof(float) * nch * 64);
+  const size_t o_cd = take(sizeof(float) * nch);
   const size_t total = off;
 
   std::vector<char> host(total, 0);
@@ -348,6 +352,11 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   put(o_ci, hb.col_idx.data(), sizeof(int) * nnz);
   put(o_hv, hb.h_val.data(), sizeof(double) * nnz);
   put(o_sv, hb.s_val.data(), sizeof(double) * nnz);
+  if (nch) {
+    put(o_cu, hb.chol_up.data(), sizeof(float) * nch * 64);
+    put(o_cr, hb.chol_row.data(), sizeof(float) * nch * 64);
+    put(o_cd, hb.chol_invd.data(), sizeof(float) * nch);
+  }
 
   gb_matrix* m = new gb_matrix();
   m->device = dev;
@@ -389,6 +398,10 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   d.s_val = reinterpret_cast<const double*>(b + o_sv);
   d.s_lam_min = hb.lam_min;
   d.s_lam_max = hb.lam_max;
+  d.chol_bw = nch ? hb.chol_bw : 0;
+  d.chol_up = nch ? reinterpret_cast<const float*>(b + o_cu) : nullptr;
+  d.chol_row = nch ? reinterpret_cast<const float*>(b + o_cr) : nullptr;
+  d.chol_invd = nch ? reinterpret_cast<const float*>(b + o_cd) : nullptr;
   *out = m;
   return GB_OK;
 }
@@ -477,6 +490,10 @@ namespace {
 // the Lanczos bounds widened by 2% on each side.
 void set_inner_method(const gb_matrix* m, const gb_solve_params* p, double itol, gbk::Args& a) {
   std::memset(&a, 0, sizeof a);
+  if (p->prec == GB_MIXED && (p->flags & 8) && m->dm.chol_bw > 0) {
+    a.inner_chol = 1;  // banded Cholesky triangular solves on both FP32 levels
+    return;
+  }
   const double lmin = m->dm.s_lam_min * 0.98, lmax = m->dm.s_lam_max * 1.02;
   if (p->prec != GB_MIXED || (p->flags & 4) || !(lmin > 0.0) || !(lmax > lmin)) return;
   const double kappa = lmax / lmin, sk = std::sqrt(kappa);
@@ -1291,6 +1308,7 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
       gbk::Args im;
       set_inner_method(m, p, p->inner_tol > 0 ? p->inner_tol : (p->prec == GB_FP64 ? 1e-14 : 1e-7), im);
       a.inner_cheb = im.inner_cheb;
+      a.inner_chol = im.inner_chol;
       a.cheb_K = im.cheb_K;
       a.cheb_c0 = im.cheb_c0;
       std::memcpy(a.cheb_A, im.cheb_A, sizeof a.cheb_A);

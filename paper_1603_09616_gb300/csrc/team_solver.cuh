@@ -59,6 +59,7 @@ struct Args {
   // Chebyshev inner iteration of the mixed path (inner_cheb = 1): K steps per
   // FP32 level with d_{k+1} = A_k d_k + B_k M^-1 r_{k+1}, d_0 = c0 M^-1 r_0.
   int inner_cheb, cheb_K;
+  int inner_chol;  // 1: the FP32 levels solve S x = r by the banded Cholesky factor
   float cheb_c0;
   float cheb_A[48], cheb_B[48];
   double* ldos;
@@ -458,6 +459,100 @@ __device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, flo
   }
 }
 
+// ------------------------------------------------------------ inner banded Cholesky, FP32
+// x = S^-1 r as L y = r, L^T x = y with the banded factor of gb_build_bsr, one
+// warp per column.  Column-oriented substitution: the partial sums of the rows
+// inside the band live in a 64-slot ring across the lanes (row k in slot
+// k mod 64, two slots per lane); each step finishes one row (its owner lane
+// scales by 1 / L(i,i), a shuffle broadcasts the value) and every other slot
+// subtracts its band entry times it, so a row costs one multiply, one
+// broadcast and one FMA on the critical path.  y is kept in the direction
+// vector d of the level (overwritten).
+__device__ void band_solve32(const Args& a, Smem& sm, const float2* __restrict__ r, float2* __restrict__ y,
+                             float2* __restrict__ x) {
+  const int W = a.W, N4 = 4 * a.m.nb, lane = threadIdx.x & 31;
+  const float* __restrict__ Lup = a.m.chol_up;
+  const float* __restrict__ Lrow = a.m.chol_row;
+  const float* __restrict__ invd = a.m.chol_invd;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int c = threadIdx.x >> 5; c < W; c += NWARP) {
+    if (!sm.act[c]) continue;
+    // forward: L y = r; the ring holds rows i .. i+63
+    float2 s0 = lane < N4 ? r[(size_t)lane * W + c] : zero;
+    float2 s1 = lane + 32 < N4 ? r[(size_t)(lane + 32) * W + c] : zero;
+    for (int i = 0; i < N4; ++i) {
+      const int so = i & 63;
+      const float2 own = (so >> 5) ? s1 : s0;
+      const float di = __ldg(invd + i);
+      float2 v = make_float2(own.x * di, own.y * di);
+      v.x = __shfl_sync(0xffffffffu, v.x, so & 31);
+      v.y = __shfl_sync(0xffffffffu, v.y, so & 31);
+      if (lane == 0) y[(size_t)i * W + c] = v;
+      const float* __restrict__ li = Lup + (size_t)i * 64;
+      {
+        const int slot = lane, t = (slot - i - 1) & 63;  // this slot holds row i + 1 + t
+        if (slot == so) {
+          s0 = i + 64 < N4 ? r[(size_t)(i + 64) * W + c] : zero;
+        } else {
+          const float l = __ldg(li + t);
+          s0.x = fmaf(-l, v.x, s0.x);
+          s0.y = fmaf(-l, v.y, s0.y);
+        }
+      }
+      {
+        const int slot = lane + 32, t = (slot - i - 1) & 63;
+        if (slot == so) {
+          s1 = i + 64 < N4 ? r[(size_t)(i + 64) * W + c] : zero;
+        } else {
+          const float l = __ldg(li + t);
+          s1.x = fmaf(-l, v.x, s1.x);
+          s1.y = fmaf(-l, v.y, s1.y);
+        }
+      }
+    }
+    __syncwarp();
+    // backward: L^T x = y; the ring holds rows i-63 .. i
+    {
+      const int base = N4 - 64;
+      const int ra = base + ((lane - base) & 63), rb = base + ((lane + 32 - base) & 63);
+      s0 = ra >= 0 ? y[(size_t)ra * W + c] : zero;
+      s1 = rb >= 0 ? y[(size_t)rb * W + c] : zero;
+    }
+    for (int i = N4 - 1; i >= 0; --i) {
+      const int so = i & 63;
+      const float2 own = (so >> 5) ? s1 : s0;
+      const float di = __ldg(invd + i);
+      float2 v = make_float2(own.x * di, own.y * di);
+      v.x = __shfl_sync(0xffffffffu, v.x, so & 31);
+      v.y = __shfl_sync(0xffffffffu, v.y, so & 31);
+      if (lane == 0) x[(size_t)i * W + c] = v;
+      const float* __restrict__ li = Lrow + (size_t)i * 64;
+      {
+        const int slot = lane, t = (i - 1 - slot) & 63;  // this slot holds row i - 1 - t
+        if (slot == so) {
+          s0 = i - 64 >= 0 ? y[(size_t)(i - 64) * W + c] : zero;
+        } else {
+          const float l = __ldg(li + t);
+          s0.x = fmaf(-l, v.x, s0.x);
+          s0.y = fmaf(-l, v.y, s0.y);
+        }
+      }
+      {
+        const int slot = lane + 32, t = (i - 1 - slot) & 63;
+        if (slot == so) {
+          s1 = i - 64 >= 0 ? y[(size_t)(i - 64) * W + c] : zero;
+        } else {
+          const float l = __ldg(li + t);
+          s1.x = fmaf(-l, v.x, s1.x);
+          s1.y = fmaf(-l, v.y, s1.y);
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0) ++sm.inner_count;
+  __syncthreads();
+}
+
 // Stores the per-real-column CG start scalars from a reduced {g^T z, ||f||^2}.
 __device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
   if (threadIdx.x < 2 * W) {
@@ -509,7 +604,9 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     block_reduce<4>(v, W, sm.rs);
     cg_start_scalars(sm, W);
   }
-  if (a.inner_cheb)
+  if (a.inner_chol)
+    band_solve32(a, sm, g, d, x);
+  else if (a.inner_cheb)
     cheb32_loop(a, sm, x, g, d, q);
   else
     cg32_loop(a, sm, x, g, d, q, itol);
@@ -564,7 +661,9 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     }
     cg_start_scalars(sm, W);  // its barrier orders the x / w writes too
   }
-  if (a.inner_cheb)
+  if (a.inner_chol)
+    band_solve32(a, sm, g, d, x);
+  else if (a.inner_cheb)
     cheb32_loop(a, sm, x, g, d, q);
   else
     cg32_loop(a, sm, x, g, d, q, itol);

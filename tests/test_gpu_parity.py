@@ -225,3 +225,20 @@ def test_correction_solve_fixes_stagnating_column(dev):
     assert (to_np(out["resid"]) <= 1e-6).all()
     ref = oracle.solve_outputs(sysm, pr["z"], pr["cols"], pr["w_rho"], pr["w_edm"])
     check_outputs(out, ref, 1e-6)
+
+
+@pytest.mark.parametrize("panel", [4, 8])
+def test_mixed_banded_cholesky_inner_solve(dev, panel):
+    # flags bit 3: the FP32 inner levels solve S x = r with the banded Cholesky
+    # factor (S's half-bandwidth is 53 here): one inner step per level, so the
+    # inner count is twice the outer count (plus the initial S^-1 b solve);
+    # outputs match the oracle.
+    system = ppv_chain(4, seed=9)  # N = 152
+    z = shift_grid(-10, 6, 40, 0.05)
+    cols = np.arange(1, system.n, 9, dtype=np.int32)
+    out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=panel, flags=8)
+    check_outputs(out, ref, 1e-6)
+    it = to_np(out["iters"])
+    inner = to_np(out["inner_iters"])
+    for p0 in range(0, len(cols), panel):
+        assert inner[p0] in (2 * it[p0 : p0 + panel].max(), 2 * (it[p0 : p0 + panel].max() + 1))
