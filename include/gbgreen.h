@@ -104,6 +104,21 @@ gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info);
 void gb_free(gb_matrix* m);
 
 /*
+ * gb_band_cholesky_to_host — the banded Cholesky factor S = L L^T that
+ * gb_build_bsr stores for the inner solve of flags bit 3, computed on the host
+ * without a GPU (for inspection and tests).  The factor is taken on the padded
+ * size N4 = 4 ceil(n/4), rows >= n being identity.  *bw receives S's
+ * half-bandwidth, or 0 when it exceeds 63 or S is not positive definite (then
+ * nothing else is written).  Caller-owned host outputs, any may be NULL:
+ *   up  [N4*64] float32: up[i*64 + t]  = L(i+1+t, i) for t < bw, else 0
+ *   row [N4*64] float32: row[i*64 + t] = L(i, i-1-t) for t < bw, else 0
+ *   invd [N4]   float32: 1 / L(i, i)
+ */
+gb_status gb_band_cholesky_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                   const double* h_val, const double* s_val, int32_t* bw,
+                                   float* up, float* row, float* invd);
+
+/*
  * gb_bsr_to_host — the builder's block form, for inspection and tests.
  *
  * Runs the same host regrouping as gb_build_bsr without touching a GPU.

@@ -11,6 +11,7 @@ from ._binding import (  # noqa: F401
     GB_MIXED,
     GBError,
     Matrix,
+    band_cholesky_to_host,
     bsr_to_host,
     load,
     pattern_offsets,

@@ -25,6 +25,7 @@ EXPORTED = (
     "gb_abi_version",
     "gb_last_error",
     "gb_bsr_to_host",
+    "gb_band_cholesky_to_host",
     "gb_build_bsr",
     "gb_matrix_get_info",
     "gb_free",
@@ -94,6 +95,9 @@ def load() -> C.CDLL:
     lib.gb_bsr_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_band_cholesky_to_host.restype = C.c_int
+    lib.gb_band_cholesky_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]
     lib.gb_build_bsr.restype = C.c_int
     lib.gb_build_bsr.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(C.c_void_p)]
@@ -162,6 +166,22 @@ def bsr_to_host(system) -> dict:
                               _ptr(bp), _ptr(bc), _ptr(bh), _ptr(bs)))
     return dict(nb=nb.value, nnzb=nnzb.value, blk_ptr=bp, blk_col=bc, blk_h=bh.reshape(-1, 4, 4),
                 blk_s=bs.reshape(-1, 4, 4))
+
+
+def band_cholesky_to_host(system) -> dict:
+    """The banded Cholesky factor of S used by the flags-bit-3 inner solve,
+    computed on the host (no GPU): bw (0 if unavailable), up / row [N4, 64],
+    invd [N4] (float32)."""
+    lib = load()
+    n, rp, ci, hv, sv = _csr(system)
+    n4 = 4 * ((int(n) + 3) // 4)
+    bw = C.c_int32()
+    up = np.zeros((n4, 64), np.float32)
+    row = np.zeros((n4, 64), np.float32)
+    invd = np.zeros(n4, np.float32)
+    _check(lib.gb_band_cholesky_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(bw), _ptr(up), _ptr(row),
+                                        _ptr(invd)))
+    return dict(bw=bw.value, up=up, row=row, invd=invd)
 
 
 def _stream_handle(stream):

@@ -288,6 +288,23 @@ gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_i
   return GB_OK;
 }
 
+gb_status gb_band_cholesky_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
+                                   const double* s_val, int32_t* bw, float* up, float* row, float* invd) {
+  clear_error();
+  if (!bw) return fail(GB_EINVAL, "bw must not be NULL");
+  HostBSR hb;
+  gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
+  if (st != GB_OK) return st;
+  band_cholesky(&hb);
+  *bw = hb.chol_bw;
+  if (hb.chol_bw > 0) {
+    if (up) std::memcpy(up, hb.chol_up.data(), sizeof(float) * hb.chol_up.size());
+    if (row) std::memcpy(row, hb.chol_row.data(), sizeof(float) * hb.chol_row.size());
+    if (invd) std::memcpy(invd, hb.chol_invd.data(), sizeof(float) * hb.chol_invd.size());
+  }
+  return GB_OK;
+}
+
 gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
                        const double* s_val, void* stream, gb_matrix** out) {
   clear_error();

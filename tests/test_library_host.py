@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import paper_1603_09616_gb300 as gbg
-from synth import TBSystem, chain_4orb, ppv_chain
+from synth import TBSystem, chain_4orb, ppv_bundle, ppv_chain
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -112,3 +112,46 @@ def test_gpu_entry_points_fail_loudly_without_a_device():
         pytest.skip("a GPU is visible")
     with pytest.raises(RuntimeError, match="no CUDA device"):
         gbg.Matrix(chain_4orb(4, seed=0))
+
+
+@pytest.mark.parametrize("maker", [lambda: chain_4orb(9, seed=1), lambda: ppv_chain(3, seed=4)])
+def test_band_cholesky_factor_reproduces_s(maker):
+    # the factor the flags-bit-3 inner solve uses: L L^T = S on the padded size
+    # (identity past n), band layout by columns (up) and rows (row) consistent
+    system = maker()
+    f = gbg.band_cholesky_to_host(system)
+    _, S = system.dense()
+    n = system.n
+    n4 = 4 * ((n + 3) // 4)
+    rows, cols = np.nonzero(np.tril(S))
+    assert f["bw"] == int((rows - cols).max())
+    bw = f["bw"]
+    L = np.zeros((n4, n4))
+    for i in range(n4):
+        L[i, i] = 1.0 / float(f["invd"][i])
+        for t in range(bw):
+            if i - 1 - t >= 0:
+                L[i, i - 1 - t] = f["row"][i, t]
+    for i in range(n4):
+        for t in range(bw):
+            if i + 1 + t < n4:
+                assert f["up"][i, t] == np.float32(L[i + 1 + t, i])
+    assert not f["up"][:, bw:].any() and not f["row"][:, bw:].any()
+    Sp = np.eye(n4)
+    Sp[:n, :n] = S
+    assert np.abs(L @ L.T - Sp).max() < 1e-5 * np.abs(Sp).max()
+    # solving with the FP32 factor is accurate to FP32 (the level's accuracy)
+    r = np.random.default_rng(0).standard_normal(n4)
+    x = np.linalg.solve(L.T, np.linalg.solve(L, r))
+    ref = np.linalg.solve(Sp, r)
+    assert np.abs(x - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+def test_band_cholesky_reports_wide_band_unavailable():
+    bundle = ppv_bundle(n_side=2, n_mono=2, seed=1)
+    _, S = bundle.dense()
+    rows, cols = np.nonzero(np.tril(S))
+    assert (rows - cols).max() > 63
+    f = gbg.band_cholesky_to_host(bundle)
+    assert f["bw"] == 0
+    assert not f["up"].any() and not f["row"].any() and not f["invd"].any()
