@@ -157,8 +157,9 @@ typedef struct {
   double tol;            /* per-pair target ||b - (z S - H) x|| / ||b|| (> 0)    */
   int32_t maxit;         /* outer (seed) iteration cap (> 0)                     */
   gb_precision prec;     /* GB_FP64 or GB_MIXED                                  */
-  double inner_tol;      /* inner-CG relative residual; <= 0: library default
-                            (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level) */
+  double inner_tol;      /* inner-solve relative residual; <= 0: library default
+                            (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level);
+                            unused by the banded Cholesky solve (flags bit 3)   */
   int32_t panel;         /* RHS columns per panel (1..32); <= 0: auto            */
   int32_t flags;         /* bit 1: keep the inner-CG vectors of a panel in shared
                             memory when they fit (fewer teams per SM);
@@ -185,8 +186,10 @@ typedef struct {
   uint8_t* converged; /* [K][nrhs] 1 if the pair met tol                        */
   double* resid;      /* [K][nrhs] recursive residual estimate at exit          */
   double* g_proj;     /* [K][P][2] optional: G_ij(z_k) (re, im) on the pattern  */
-  int32_t* inner_iters; /* [nrhs] inner-CG iterations of the column's panel,
-                           summed over the whole solve (all refinement levels) */
+  int32_t* inner_iters; /* [nrhs] inner steps of the column's panel summed over
+                           the whole solve and all refinement levels: CG
+                           iterations, Chebyshev steps, or one per level for
+                           the banded Cholesky solve (flags bit 3)            */
   int32_t* col_status;  /* [nrhs] bit flags per column: 1 COCG breakdown, 2 S not
                            SPD, 4 a shift missed tol, 8 inner CG hit its cap   */
 } gb_outputs;
