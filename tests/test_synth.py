@@ -55,3 +55,19 @@ def test_uneven_chain_ranges():
     for sysm, k in chains:
         assert 2 * 38 <= sysm.n <= 50 * 38
         assert 32 <= k <= 256
+
+
+def test_uneven_batch_is_deterministic():
+    # the GPU correction tests address chains of this batch by index
+    from synth import uneven_batch
+
+    systems, problems = uneven_batch(eta=0.02)
+    assert len(systems) == 512
+    assert (systems[331].n, len(problems[331]["z"])) == (228, 115)
+    assert (systems[69].n, len(problems[69]["z"])) == (570, 183)
+    for s, p in zip(systems[:20], problems[:20]):
+        assert 76 <= s.n <= 1900 and 32 <= len(p["z"]) <= 256
+        assert p["cols"][0] == 0 and len(set(p["cols"].tolist())) == 2
+        assert np.allclose(p["z"].imag, 0.02)
+    again, _ = uneven_batch(eta=0.02)
+    assert np.array_equal(again[331].h_val, systems[331].h_val)
