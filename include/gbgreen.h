@@ -14,9 +14,11 @@
  *
  * Solver: one seed Krylov space of A = S^{-1} H built by a conjugate
  * orthogonal CG (COCG) in the S-bilinear form, shared by every shift through
- * the collinear-residual recurrence; S^{-1} is applied by an inner
- * block-Jacobi-preconditioned CG.  The paper defers the method's details to
- * its references; the recurrences used are the standard shifted COCG ones.
+ * the collinear-residual recurrence.  S^{-1} is applied exactly by a
+ * block-bidiagonal Cholesky factor of S where S's half-bandwidth is at most 63
+ * (chains), else by an inner block-Jacobi-preconditioned iteration (CG, or
+ * Chebyshev in the mixed path).  The paper defers the method's details to its
+ * references; the recurrences used are the standard shifted COCG ones.
  *
  * Conventions for every entry point:
  *   - Return value: GB_OK (0) or a negative gb_status; gb_last_error() gives a
@@ -38,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GB_ABI_VERSION 1
+#define GB_ABI_VERSION 2
 
 typedef enum {
   GB_OK = 0,
@@ -52,7 +54,8 @@ typedef enum {
   GB_ENOCONV = -6,     /* at least one (shift, column) pair did not reach tol
                           within maxit; all outputs are still written and
                           `converged` tells which pairs met tol              */
-  GB_ETIMEOUT = -7     /* reserved: a bounded device wait gave up             */
+  GB_ETIMEOUT = -7     /* a bounded device wait (a staged factor tile of the
+                          exact inner solve) gave up; outputs are unreliable */
 } gb_status;
 
 typedef enum {
@@ -71,9 +74,11 @@ typedef struct {
   int32_t max_row;    /* longest pattern row (max |R_j|)                      */
   int32_t block;      /* block size (4)                                       */
   int32_t device;     /* CUDA device ordinal holding the matrix               */
-  int32_t reserved;
+  int32_t factor_bw;  /* S's half-bandwidth when the exact factor inner solve
+                         is available (<= 63), else 0                        */
   double s_lam_min;   /* extreme eigenvalues of M^-1 S, M the 4x4 block       */
   double s_lam_max;   /* diagonal of S (Lanczos estimates at build time)      */
+  int64_t factor_nblk; /* 64-row blocks of that factor (0: none)              */
 } gb_matrix_info;
 
 /*
@@ -104,19 +109,23 @@ gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info);
 void gb_free(gb_matrix* m);
 
 /*
- * gb_band_cholesky_to_host — the banded Cholesky factor S = L L^T that
- * gb_build_bsr stores for the inner solve of flags bit 3, computed on the host
- * without a GPU (for inspection and tests).  The factor is taken on the padded
- * size N4 = 4 ceil(n/4), rows >= n being identity.  *bw receives S's
- * half-bandwidth, or 0 when it exceeds 63 or S is not positive definite (then
- * nothing else is written).  Caller-owned host outputs, any may be NULL:
- *   up  [N4*64] float32: up[i*64 + t]  = L(i+1+t, i) for t < bw, else 0
- *   row [N4*64] float32: row[i*64 + t] = L(i, i-1-t) for t < bw, else 0
- *   invd [N4]   float32: 1 / L(i, i)
+ * gb_block_factor_to_host — the factor of S that the exact inner solve uses,
+ * computed on the host without a GPU (for inspection and tests).  S^{-1} is
+ * applied once per Krylov iteration (the S-inner-product recurrence of the
+ * shifted equations, Introduction); with half-bandwidth bw <= 63 the Cholesky
+ * factor S = L L^T, cut into 64-row blocks (rows past n are identity), is
+ * block lower bidiagonal with diagonal blocks D_i and sub-diagonal blocks C_i.
+ * *bw receives S's half-bandwidth and *nblk the block count ceil(4 ceil(n/4)
+ * / 64), or both 0 when bw exceeds 63 or S is not positive definite.
+ * `factor` (host, caller-owned, may be NULL) receives 4 * nblk * 4096 doubles:
+ * four arrays [nblk][64][64], each block stored k-major (entry (r, k) of the
+ * block's matrix at k * 64 + r): D_i^-1, D_i^-T, E_i = D_i^-1 C_i and
+ * F_i = D_i^-T C_{i+1}^T.  The solve is y_i = D_i^-1 f_i - E_i y_{i-1},
+ * x_i = D_i^-T y_i - F_i x_{i+1}.
  */
-gb_status gb_band_cholesky_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
-                                   const double* h_val, const double* s_val, int32_t* bw,
-                                   float* up, float* row, float* invd);
+gb_status gb_block_factor_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                  const double* h_val, const double* s_val, int32_t* bw, int64_t* nblk,
+                                  double* factor);
 
 /*
  * gb_bsr_to_host — the builder's block form, for inspection and tests.
@@ -135,8 +144,9 @@ gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_i
 /*
  * gb_spmm — Y = A X for A = H (which = 0) or S (which = 1).
  *
- * The sparse products of the Krylov recurrence (one with H per iteration, one
- * with S per inner-CG iteration).  X and Y are device arrays of n rows x w
+ * The sparse products of the Krylov recurrence for (z S - H) x = b
+ * (Introduction: the order-N cost rests on sparse H and S; one product with H
+ * per iteration, one with S per inner-iteration step).  X and Y are device arrays of n rows x w
  * complex columns, row-major with interleaved (re, im): element (i, c) at
  * [2*(i*w + c)] (re) and [2*(i*w + c) + 1] (im).  prec = GB_FP64: double
  * arrays and FP64 arithmetic; GB_MIXED: float arrays, FP32 arithmetic with
@@ -144,6 +154,22 @@ gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_i
  */
 gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t w,
                   const void* x, void* y, void* stream);
+
+/*
+ * gb_apply_sinv — Y = S^{-1} X with the exact block-bidiagonal Cholesky factor.
+ *
+ * The inner solve of the Krylov recurrence: the S-bilinear COCG applies S^{-1}
+ * once per iteration to the product H p (the overlap S of the generalized
+ * equations, Introduction).  On its own here, for tests and timing.  X and Y:
+ * device arrays of n rows x w complex columns, layout as in gb_spmm;
+ * prec = GB_FP64: double, one FP64 factor solve (exact to rounding);
+ * GB_MIXED: float, one FP32 factor solve (no refinement: ~4e-7 relative).
+ * w in {1, 2, 4, 8, 16, 32}.  GB_EINVAL if the matrix has no factor (S's
+ * half-bandwidth above 63).  Allocates its scratch on `stream` (stream-ordered
+ * allocator) and frees it; synchronous.
+ */
+gb_status gb_apply_sinv(const gb_matrix* m, gb_precision prec, int32_t w, const void* x, void* y,
+                        void* stream);
 
 typedef struct {
   int32_t nshift;        /* K >= 1                                               */
@@ -157,18 +183,26 @@ typedef struct {
   double tol;            /* per-pair target ||b - (z S - H) x|| / ||b|| (> 0)    */
   int32_t maxit;         /* outer (seed) iteration cap (> 0)                     */
   gb_precision prec;     /* GB_FP64 or GB_MIXED                                  */
-  double inner_tol;      /* inner-solve relative residual; <= 0: library default
-                            (FP64: 1e-14; mixed: 1e-7 per FP32 refinement level);
-                            unused by the banded Cholesky solve (flags bit 3)   */
+  double inner_tol;      /* iterative inner solve's relative residual; <= 0:
+                            library default (FP64: 1e-14; mixed: 1e-7 per FP32
+                            refinement level); unused by the exact factor solve */
   int32_t panel;         /* RHS columns per panel (1..32); <= 0: auto            */
-  int32_t flags;         /* bit 1: keep the inner-CG vectors of a panel in shared
-                            memory when they fit (fewer teams per SM);
-                            bit 2: mixed path uses CG instead of the Chebyshev
-                            inner iteration for its FP32 levels;
-                            bit 3: mixed path solves its FP32 levels with the
-                            banded Cholesky factor of S (two triangular solves,
-                            no iteration) when S's half-bandwidth is <= 63;
-                            otherwise the bit is ignored                     */
+  int32_t flags;         /* Inner solve S w = u.  Default: the exact
+                            block-bidiagonal Cholesky solve where S's
+                            half-bandwidth is <= 63 (FP64: one solve; mixed: two
+                            FP32 solves around a float-float residual), else
+                            an iteration (FP64: CG; mixed: Chebyshev).
+                            bit 1: keep the inner-iteration vectors of a panel
+                            in shared memory when they fit (iterations only);
+                            bit 2: iterate with CG instead of the factor solve
+                            (and instead of Chebyshev in the mixed path);
+                            bit 4: mixed path iterates with Chebyshev instead
+                            of the factor solve;
+                            bit 5: mixed path forms H p as an unrefined FP32
+                            product (faster, but its rounding makes the
+                            recursive residual estimate drift below the true
+                            residual: pair it with gb_true_residual);
+                            other bits are ignored                           */
   int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
   int32_t reserved;
 } gb_solve_params;
@@ -189,9 +223,10 @@ typedef struct {
   int32_t* inner_iters; /* [nrhs] inner steps of the column's panel summed over
                            the whole solve and all refinement levels: CG
                            iterations, Chebyshev steps, or one per level for
-                           the banded Cholesky solve (flags bit 3)            */
+                           the exact factor solve                            */
   int32_t* col_status;  /* [nrhs] bit flags per column: 1 COCG breakdown, 2 S not
-                           SPD, 4 a shift missed tol, 8 inner CG hit its cap   */
+                           SPD, 4 a shift missed tol, 8 inner CG hit its cap,
+                           16 a bounded wait for a factor tile gave up        */
 } gb_outputs;
 
 /*
@@ -203,8 +238,10 @@ size_t gb_solve_workspace_size(const gb_matrix* m, const gb_solve_params* p);
 /*
  * gb_solve_plan — the launch plan gb_shifted_solve would use for (m, p):
  * plan[0] = RHS columns per panel, plan[1] = teams (CTAs) launched,
- * plan[2] = 1 if the inner-CG vectors live in shared memory, plan[3] = their
- * dynamic shared-memory bytes.  `plan` is a caller-owned host int32[4].
+ * plan[2] = 1 if the inner-iteration vectors live in shared memory,
+ * plan[3] = dynamic shared-memory bytes per team, plan[4] = inner solve
+ * (0 CG, 1 Chebyshev, 2 exact factor), plan[5] = teams resident per SM.
+ * `plan` is a caller-owned host int32[6].
  */
 gb_status gb_solve_plan(const gb_matrix* m, const gb_solve_params* p, int32_t* plan);
 
@@ -228,9 +265,14 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
  * breakdown or an indefinite S are left alone).  The paper's equation is the
  * same (Introduction); the correction is this library's answer to shifted
  * COCG's limited attainable accuracy: each such column is solved again alone,
- * in plain FP64, with its worst unconverged shift (largest resid) as the seed,
- * and its ldos, rho, edm, q, e_loc, iters, inner_iters, converged, resid,
- * g_proj and col_status entries in `out` are overwritten.
+ * in plain FP64 (exact factor inner solve where available), with its worst
+ * unconverged shift (largest resid) as the seed.  While shifts still miss
+ * tol, the worst remaining one seeds the next solve (six seeds at most), and
+ * every shift keeps the result of the seed that served it best (its G_ij(z_k)
+ * on the pattern row; rho, edm, q and e_loc are formed from those).  The
+ * column's ldos, rho, edm, q, e_loc, iters and inner_iters (summed over the
+ * seeds), converged, resid, g_proj and col_status entries in `out` are
+ * overwritten.
  *
  * `p` and `out` are those of the first solve (out->col_status and out->resid
  * are required).  `workspace`: caller-owned device memory of at least
@@ -247,9 +289,44 @@ gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, c
 size_t gb_correct_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t want_g);
 
 /*
+ * gb_true_residual — FP64 true-residual check of a solve's columns.
+ *
+ * The shifted recurrence reports the recursive estimate ||rt_n|| / |pi^k_n|
+ * of ||b - (z_k S - H) x^k|| (Introduction: the generalized shifted
+ * equations); it equals the true residual only while every inner solve is
+ * exact, so an inexact S^{-1} (an iterative inner solve, or reduced
+ * precision) can report convergence that the true residual denies.  This call
+ * re-runs the columns p->rhs_cols[ver[v]], v < nver, with the solve's own
+ * parameters (same precision, seed, inner solve), keeping the history r_m on
+ * every row, forms x^k = sum_m c^k_m r_m for every shift (a complex FP64
+ * product of the history with the recurrence's coefficients) and evaluates
+ * ||e_j - (z_k S - H) x^k||_2 in FP64 from the scalar CSR of H and S.
+ *   nver        1..1024 columns to check (ver: host [nver], 0 <= ver[v] < nrhs)
+ *   resid_true  device [K][nver] FP64 true residuals (caller-owned)
+ *   out         NULL, or the outputs of the solve being checked: for every
+ *               checked column whose true residual misses tol on some shift,
+ *               col_status gets bit 4 and resid / converged take the true
+ *               values, so gb_correct_unconverged re-solves it
+ *   workspace   gb_true_residual_workspace_size(m, p, nver) bytes, 256-byte
+ *               aligned: the history of every checked column, (maxit + 1) x
+ *               4 ceil(n/4) x 16 bytes each, plus the solutions x^k
+ *   nflagged    host, may be NULL: columns newly marked in `out`
+ * Synchronous.  Costs one solve of the checked columns plus the product.
+ */
+gb_status gb_true_residual(const gb_matrix* m, const gb_solve_params* p, int32_t nver, const int32_t* ver,
+                           double* resid_true, const gb_outputs* out, void* workspace, size_t workspace_bytes,
+                           void* stream, int32_t* nflagged);
+
+/* Bytes of workspace gb_true_residual needs (0: invalid parameters). */
+size_t gb_true_residual_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t nver);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
- * Each system s solves (z_k S_s - H_s) x = e_j for its own shifts and columns
+ * The shifted equations of the Introduction for many independent structures
+ * at once (the Quantum molecular dynamics section solves one polymer bundle
+ * per MD step; independent chains of uneven length are this entry point's
+ * unit of work).  Each system s solves (z_k S_s - H_s) x = e_j for its own shifts and columns
  * (params[s]) on its own matrix mats[s] and writes its own outputs outs[s];
  * all systems share one precision and one device.  Work items are (system,
  * panel of `panel` columns) pairs taken from a device counter, largest systems
@@ -267,9 +344,9 @@ size_t gb_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, con
 
 /*
  * gb_tune_panel_batched — autotuner for the batched panel width: runs the
- * batch with every maxit capped at probe_maxit for panel widths {4, 8, 16, 32},
+ * batch with every maxit capped at probe_maxit for panel widths {8, 16, 32},
  * times each launch on `stream`, and returns the fastest in *best_panel
- * (times_ms: optional host float[4], -1 for a width that did not fit the
+ * (times_ms: optional host float[3], -1 for a width that did not fit the
  * workspace).  The outputs are overwritten by the probe runs.
  */
 gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
@@ -290,8 +367,7 @@ gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, cons
  * staged in fixed host buffers.  No cudaMalloc, cudaFree or other allocating
  * routine is called.
  *   - The first call on a device looks up the scratch's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture on the device.
+ *     per device, with that device current).
  *   - Problems whose scratch exceeds the array, or with nrhs > 4096, are
  *     rejected (GB_ENOMEM / GB_EINVAL) with a message naming the limit; the
  *     number of concurrent teams is reduced when that lets the problem fit
@@ -300,7 +376,8 @@ gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, cons
  *     re-initialises everything it reads (the work counter is cleared from
  *     the host).  Calls whose GPU work overlaps (other streams, other host
  *     threads) race on the array: serialise them.
- * Synchronous.
+ * Synchronous: the call waits on `stream` for its own work (it reads the
+ * per-column status back) before it returns.
  */
 gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, const gb_outputs* out,
                                   void* stream);

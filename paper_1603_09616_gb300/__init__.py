@@ -11,7 +11,7 @@ from ._binding import (  # noqa: F401
     GB_MIXED,
     GBError,
     Matrix,
-    band_cholesky_to_host,
+    block_factor_to_host,
     bsr_to_host,
     load,
     pattern_offsets,
@@ -19,5 +19,6 @@ from ._binding import (  # noqa: F401
     shifted_solve_batched,
     shifted_solve_static,
     solve_plan,
+    true_residual,
     workspace_bytes,
 )

@@ -25,17 +25,22 @@ EXPORTED = (
     "gb_abi_version",
     "gb_last_error",
     "gb_bsr_to_host",
-    "gb_band_cholesky_to_host",
+    "gb_block_factor_to_host",
     "gb_build_bsr",
     "gb_matrix_get_info",
     "gb_free",
     "gb_spmm",
+    "gb_apply_sinv",
     "gb_solve_workspace_size",
     "gb_solve_plan",
     "gb_shifted_solve",
     "gb_shifted_solve_static",
     "gb_static_scratch_bytes",
     "gb_shifted_solve_batched",
+    "gb_true_residual",
+    "gb_true_residual_workspace_size",
+    "gb_correct_unconverged",
+    "gb_correct_workspace_size",
     "gb_batched_workspace_size",
     "gb_tune_panel_batched",
 )
@@ -49,8 +54,8 @@ class GBError(RuntimeError):
 
 class MatrixInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64), ("nnzb", C.c_int64),
-                ("max_row", C.c_int32), ("block", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32),
-                ("s_lam_min", C.c_double), ("s_lam_max", C.c_double)]
+                ("max_row", C.c_int32), ("block", C.c_int32), ("device", C.c_int32), ("factor_bw", C.c_int32),
+                ("s_lam_min", C.c_double), ("s_lam_max", C.c_double), ("factor_nblk", C.c_int64)]
 
 
 class SolveParams(C.Structure):
@@ -95,9 +100,9 @@ def load() -> C.CDLL:
     lib.gb_bsr_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
-    lib.gb_band_cholesky_to_host.restype = C.c_int
-    lib.gb_band_cholesky_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                             C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_block_factor_to_host.restype = C.c_int
+    lib.gb_block_factor_to_host.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_void_p]
     lib.gb_build_bsr.restype = C.c_int
     lib.gb_build_bsr.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(C.c_void_p)]
@@ -107,6 +112,8 @@ def load() -> C.CDLL:
     lib.gb_free.argtypes = [C.c_void_p]
     lib.gb_spmm.restype = C.c_int
     lib.gb_spmm.argtypes = [C.c_void_p, C.c_int32, C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_apply_sinv.restype = C.c_int
+    lib.gb_apply_sinv.argtypes = [C.c_void_p, C.c_int, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.gb_solve_workspace_size.restype = C.c_size_t
     lib.gb_solve_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
     lib.gb_solve_plan.restype = C.c_int
@@ -119,6 +126,11 @@ def load() -> C.CDLL:
                                            C.c_size_t, C.c_void_p, C.POINTER(C.c_int32)]
     lib.gb_correct_workspace_size.restype = C.c_size_t
     lib.gb_correct_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
+    lib.gb_true_residual.restype = C.c_int
+    lib.gb_true_residual.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32)]
+    lib.gb_true_residual_workspace_size.restype = C.c_size_t
+    lib.gb_true_residual_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
     lib.gb_shifted_solve_static.restype = C.c_int
     lib.gb_shifted_solve_static.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p]
     lib.gb_static_scratch_bytes.restype = C.c_size_t
@@ -168,20 +180,21 @@ def bsr_to_host(system) -> dict:
                 blk_s=bs.reshape(-1, 4, 4))
 
 
-def band_cholesky_to_host(system) -> dict:
-    """The banded Cholesky factor of S used by the flags-bit-3 inner solve,
-    computed on the host (no GPU): bw (0 if unavailable), up / row [N4, 64],
-    invd [N4] (float32)."""
+def block_factor_to_host(system) -> dict:
+    """The block-bidiagonal Cholesky factor of S used by the exact inner solve,
+    computed on the host (no GPU): bw and nblk (both 0 if unavailable), and the
+    four [nblk, 64, 64] arrays Dinv, DinvT, E, F with entry (r, k) of each
+    block at [blk, k, r] (k-major, as stored on the device)."""
     lib = load()
     n, rp, ci, hv, sv = _csr(system)
-    n4 = 4 * ((int(n) + 3) // 4)
-    bw = C.c_int32()
-    up = np.zeros((n4, 64), np.float32)
-    row = np.zeros((n4, 64), np.float32)
-    invd = np.zeros(n4, np.float32)
-    _check(lib.gb_band_cholesky_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(bw), _ptr(up), _ptr(row),
-                                        _ptr(invd)))
-    return dict(bw=bw.value, up=up, row=row, invd=invd)
+    bw, nblk = C.c_int32(), C.c_int64()
+    _check(lib.gb_block_factor_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(bw), C.byref(nblk), None))
+    nb_ = int(nblk.value)
+    f = np.zeros((4, nb_, 64, 64), np.float64)
+    if nb_:
+        _check(lib.gb_block_factor_to_host(n, _ptr(rp), _ptr(ci), _ptr(hv), _ptr(sv), C.byref(bw), C.byref(nblk),
+                                           _ptr(f)))
+    return dict(bw=int(bw.value), nblk=nb_, dinv=f[0], dinvt=f[1], e=f[2], f=f[3])
 
 
 def _stream_handle(stream):
@@ -238,6 +251,20 @@ class Matrix:
         return y
 
 
+    def apply_sinv(self, x, prec: str = "fp64", out=None, stream=None):
+        """Y = S^-1 X by the exact factor solve; X complex [n, w] on the GPU,
+        w in {1, 2, 4, 8, 16, 32} (FP32: one unrefined solve)."""
+        import torch
+
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        x = x.to(dt).contiguous()
+        assert x.is_cuda and x.dim() == 2 and x.shape[0] == self.n
+        y = out if out is not None else torch.empty_like(x)
+        _check(load().gb_apply_sinv(self._h, GB_FP64 if prec == "fp64" else GB_MIXED, int(x.shape[1]),
+                                    C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), _stream_handle(stream)))
+        return y
+
+
 def pattern_offsets(system, cols) -> np.ndarray:
     cols = np.asarray(cols, dtype=np.int64)
     m = system.row_ptr[cols + 1] - system.row_ptr[cols]
@@ -289,22 +316,28 @@ def solve_plan(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", panel=0
     """Launch plan of gb_shifted_solve: panel width, teams, shared-memory use."""
     keep = []
     p = _params(z, cols, tol, maxit, prec, None, None, 0.0, panel, -1, keep, flags)
-    plan = np.zeros(4, np.int32)
+    plan = np.zeros(6, np.int32)
     _check(load().gb_solve_plan(mat.handle, C.byref(p), _ptr(plan)))
-    return dict(panel=int(plan[0]), teams=int(plan[1]), cg_smem=bool(plan[2]), dyn_smem=int(plan[3]))
+    return dict(panel=int(plan[0]), teams=int(plan[1]), cg_smem=bool(plan[2]), dyn_smem=int(plan[3]),
+                inner=("cg", "chebyshev", "factor")[int(plan[4])], teams_per_sm=int(plan[5]))
 
 
 def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
                   inner_tol=0.0, panel=0, seed_shift=-1, want_g=False, workspace=None, stream=None, flags=0,
-                  raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD), correct=False):
+                  raise_on=(GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD), correct=False, verify=None):
     """Solve (z_k S - H) x = e_j for all shifts and columns; returns device tensors.
 
     Keys: ldos [K, nrhs], rho / edm [P], q / e_loc [nrhs], iters [nrhs],
     converged [K, nrhs] (uint8), resid [K, nrhs], g_proj [K, P] complex (if
-    want_g), off [nrhs+1] (host, packed offsets), status (int).  With
-    ``correct=True`` a GB_ENOCONV result is passed to gb_correct_unconverged
-    (FP64 re-solve of the failing columns with a switched seed); ``corrected``
-    then holds the number of columns it fixed.
+    want_g), off [nrhs+1] (host, packed offsets), status (int).
+
+    ``verify``: indices into ``cols`` (or True for all) whose FP64 true
+    residual is checked after the solve (gb_true_residual); ``resid_true``
+    [K, len(verify)] then holds it, and columns that miss tol become
+    unconverged in the outputs.  With ``correct=True`` a GB_ENOCONV result
+    (from the solve or the check) is passed to gb_correct_unconverged (FP64
+    re-solve of the failing columns with a switched seed); ``corrected`` then
+    holds the number of columns it fixed.
     """
     import torch
 
@@ -346,6 +379,27 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
     res["message"] = lib.gb_last_error().decode()
     res["off"] = off
     res["workspace"] = workspace
+    if verify is not None and st in (GB_OK, GB_ENOCONV):
+        ver = np.arange(nrhs, dtype=np.int32) if verify is True else np.ascontiguousarray(verify, dtype=np.int32)
+        nver = len(ver)
+        vneed = lib.gb_true_residual_workspace_size(mat.handle, C.byref(p), nver)
+        if vneed == 0:
+            raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+        vws = torch.empty(int(vneed), dtype=torch.uint8, device=dev)
+        rtrue = torch.empty((K, nver), dtype=torch.float64, device=dev)
+        nflag = C.c_int32(0)
+        vst = lib.gb_true_residual(mat.handle, C.byref(p), nver, _ptr(ver), C.c_void_p(rtrue.data_ptr()),
+                                   C.byref(o), C.c_void_p(vws.data_ptr()), C.c_size_t(vws.numel()),
+                                   _stream_handle(stream), C.byref(nflag))
+        _check(vst)
+        del vws
+        res["resid_true"] = rtrue
+        res["verified"] = ver
+        res["flagged"] = int(nflag.value)
+        if nflag.value > 0:
+            st = GB_ENOCONV
+            res["status"] = st
+            res["message"] = f"{nflag.value} checked column(s) miss tol by their true residual"
     if correct and st == GB_ENOCONV:
         cneed = lib.gb_correct_workspace_size(mat.handle, C.byref(p), int(want_g))
         if cneed == 0:
@@ -360,6 +414,28 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
         res["message"] = lib.gb_last_error().decode()
         res["corrected"] = int(fixed.value)
     return res
+
+
+def true_residual(mat: Matrix, z, cols, verify, tol=1e-10, maxit=1000, prec="fp64", inner_tol=0.0, panel=0,
+                  seed_shift=-1, flags=0, stream=None):
+    """FP64 true residuals ||e_j - (z_k S - H) x^k|| [K, len(verify)] of the
+    columns cols[verify] as the solve with these parameters produces them
+    (gb_true_residual: the columns are re-run with their full history)."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    p = _params(z, cols, tol, maxit, prec, None, None, inner_tol, panel, seed_shift, keep, flags)
+    lib = load()
+    ver = np.ascontiguousarray(verify, dtype=np.int32)
+    need = lib.gb_true_residual_workspace_size(mat.handle, C.byref(p), len(ver))
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    out = torch.empty((p.nshift, len(ver)), dtype=torch.float64, device=dev)
+    _check(lib.gb_true_residual(mat.handle, C.byref(p), len(ver), _ptr(ver), C.c_void_p(out.data_ptr()), None,
+                                C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), _stream_handle(stream), None))
+    return out
 
 
 def shifted_solve_static(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rho=None, w_edm=None,
@@ -431,7 +507,7 @@ def _alloc_outputs(mat, K, cols, w_rho, w_edm, want_g, dev):
 
 
 def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, workspace=None, stream=None,
-                          tune_probe_maxit=0, correct=False):
+                          tune_probe_maxit=0, correct=False, flags=0):
     """Solve many independent systems in one persistent launch.
 
     ``problems`` is a list of dicts with keys z, cols, tol, maxit and optional
@@ -453,7 +529,7 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
     results = []
     for s_, (mat, pr) in enumerate(zip(mats, problems)):
         p = _params(pr["z"], pr["cols"], pr["tol"], pr["maxit"], prec, pr.get("w_rho"), pr.get("w_edm"), 0.0,
-                    panel, -1, keep)
+                    panel, -1, keep, flags)
         params[s_] = p
         res, o = _alloc_outputs(mat, len(pr["z"]), pr["cols"], pr.get("w_rho"), pr.get("w_edm"), want_g, dev)
         outs[s_] = o
@@ -464,10 +540,10 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
         probe = (SolveParams * nsys)(*params)
         for q in range(nsys):
             probe[q].maxit = min(probe[q].maxit, tune_probe_maxit)
-        need = max(lib.gb_batched_workspace_size(nsys, handles, probe, w, int(want_g)) for w in (4, 8, 16, 32))
+        need = max(lib.gb_batched_workspace_size(nsys, handles, probe, w, int(want_g)) for w in (8, 16, 32))
         tws = torch.empty(int(need), dtype=torch.uint8, device=dev)
         best = C.c_int32()
-        times = np.zeros(4, np.float32)
+        times = np.zeros(3, np.float32)
         _check(lib.gb_tune_panel_batched(nsys, handles, probe, outs, int(tune_probe_maxit),
                                          C.c_void_p(tws.data_ptr()), C.c_size_t(tws.numel()),
                                          _stream_handle(stream), C.byref(best), _ptr(times)))

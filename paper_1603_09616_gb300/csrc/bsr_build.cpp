@@ -265,13 +265,22 @@ void preconditioned_s_bounds(HostBSR* hb) {
   hb->lam_max = bisect(m - 1);
 }
 
-// Banded Cholesky of S for an exact S^-1 in the mixed path (triangular solves
-// instead of an iteration).  S's entries come from the 4x4 blocks; rows past n
-// (block padding) are identity.  Plain column-by-column factorisation inside the
-// band, FP64, then rounded to FP32 for the device; skipped (chol_bw = 0) when the
+// Block-bidiagonal form of the banded Cholesky factor of S, for an exact S^-1
+// (triangular solves instead of an iteration).  S's entries come from the 4x4
+// blocks; rows past n (block padding) and past 4 nb (64-row padding) are
+// identity.  The band factor S = L L^T is taken column by column in FP64; with
+// half-bandwidth bw <= 63, L cut into 64-row blocks is block lower bidiagonal:
+// diagonal blocks D_i (lower triangular) and sub-diagonal blocks C_i whose
+// nonzeros sit in their last bw columns.  The solve then reads
+//   L y = r  :  y_i = D_i^-1 r_i - E_i y_{i-1},      E_i = D_i^-1 C_i,
+//   L^T x = y:  x_i = D_i^-T y_i - F_i x_{i+1},      F_i = D_i^-T C_{i+1}^T,
+// where every D_i^-1 r_i is independent of the others and only the E / F
+// products form the sequential chain.  Skipped (bf_bw = 0) when the
 // half-bandwidth exceeds 63 or a pivot is not positive.
-void band_cholesky(HostBSR* hb) {
-  hb->chol_bw = 0;
+void block_factor(HostBSR* hb) {
+  hb->bf_bw = 0;
+  hb->bf_nblk = 0;
+  hb->bf.clear();
   const int64_t n4 = 4 * hb->nb, n = hb->n;
   int64_t bw = 0;
   for (int64_t I = 0; I < hb->nb; ++I)
@@ -310,17 +319,61 @@ void band_cholesky(HostBSR* hb) {
       }
     }
   }
-  hb->chol_up.assign((size_t)n4 * 64, 0.f);
-  hb->chol_row.assign((size_t)n4 * 64, 0.f);
-  hb->chol_invd.assign((size_t)n4, 0.f);
-  for (int64_t i = 0; i < n4; ++i) {
-    hb->chol_invd[i] = (float)(1.0 / at(i, i));
-    for (int64_t t = 0; t < bw; ++t) {
-      if (i + 1 + t < n4) hb->chol_up[(size_t)i * 64 + t] = (float)at(i + 1 + t, i);
-      if (i - 1 - t >= 0) hb->chol_row[(size_t)i * 64 + t] = (float)at(i, i - 1 - t);
+  // L(i, j) on the 64-row padded size (identity past 4 nb)
+  auto Lget = [&](int64_t i, int64_t j) -> double {
+    if (i >= n4 || j >= n4) return i == j ? 1.0 : 0.0;
+    if (j > i || i - j > bw) return 0.0;
+    return at(i, j);
+  };
+  const int64_t nblk = (n4 + 63) / 64;
+  const size_t T = 4096, part = (size_t)nblk * T;
+  hb->bf.assign(4 * part, 0.0);
+  double* df = hb->bf.data();
+  double* db = df + part;
+  double* ef = db + part;
+  double* fb = ef + part;
+  std::vector<double> D(T), Di(T), C(T);
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    const int64_t base = 64 * blk;
+    for (int r = 0; r < 64; ++r)
+      for (int c = 0; c < 64; ++c) D[r * 64 + c] = c <= r ? Lget(base + r, base + c) : 0.0;
+    // Di = D^-1 by forward substitution on each unit column
+    std::fill(Di.begin(), Di.end(), 0.0);
+    for (int c = 0; c < 64; ++c)
+      for (int r = c; r < 64; ++r) {
+        double s = (r == c) ? 1.0 : 0.0;
+        for (int k = c; k < r; ++k) s -= D[r * 64 + k] * Di[k * 64 + c];
+        Di[r * 64 + c] = s / D[r * 64 + r];
+      }
+    // k-major storage: M[k * 64 + r] = (matrix)[r][k]
+    for (int k = 0; k < 64; ++k)
+      for (int r = 0; r < 64; ++r) {
+        df[blk * T + k * 64 + r] = Di[r * 64 + k];
+        db[blk * T + k * 64 + r] = Di[k * 64 + r];
+      }
+    if (blk > 0) {  // E = Di C_blk, C_blk = L(block blk, block blk-1)
+      for (int r = 0; r < 64; ++r)
+        for (int c = 0; c < 64; ++c) C[r * 64 + c] = Lget(base + r, base - 64 + c);
+      for (int r = 0; r < 64; ++r)
+        for (int k = 0; k < 64; ++k) {
+          double s = 0.0;
+          for (int q = 0; q <= r; ++q) s += Di[r * 64 + q] * C[q * 64 + k];
+          ef[blk * T + k * 64 + r] = s;
+        }
+    }
+    if (blk + 1 < nblk) {  // F = Di^T C_{blk+1}^T, C_{blk+1} = L(block blk+1, block blk)
+      for (int r = 0; r < 64; ++r)
+        for (int c = 0; c < 64; ++c) C[r * 64 + c] = Lget(base + 64 + r, base + c);
+      for (int r = 0; r < 64; ++r)
+        for (int k = 0; k < 64; ++k) {
+          double s = 0.0;
+          for (int q = r; q < 64; ++q) s += Di[q * 64 + r] * C[k * 64 + q];
+          fb[blk * T + k * 64 + r] = s;
+        }
     }
   }
-  hb->chol_bw = (int32_t)bw;
+  hb->bf_bw = (int32_t)bw;
+  hb->bf_nblk = nblk;
 }
 
 }  // namespace gb

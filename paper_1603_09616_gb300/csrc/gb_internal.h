@@ -22,12 +22,14 @@ struct HostBSR {
   std::vector<int32_t> col_idx;
   std::vector<double> h_val, s_val;
   double lam_min = 0.0, lam_max = 0.0;  // spectrum bounds of M^-1 S (block Jacobi M)
-  // Banded Cholesky S = L L^T on the padded size 4 nb (rows >= n are identity),
-  // FP32, when S's half-bandwidth chol_bw is at most 63 (0: not available):
-  // chol_up[i*64 + t] = L(i+1+t, i), chol_row[i*64 + t] = L(i, i-1-t), zero
-  // outside the band; chol_invd[i] = 1 / L(i, i).
-  int32_t chol_bw = 0;
-  std::vector<float> chol_up, chol_row, chol_invd;
+  // Block-bidiagonal form of the banded Cholesky factor S = L L^T on 64-row
+  // blocks (see block_factor), FP64, when S's half-bandwidth bf_bw is at most
+  // 63 (0: not available).  bf holds four [bf_nblk][64][64] arrays, each
+  // stored k-major (entry (r, k) of the block's matrix at k * 64 + r):
+  // D_i^-1, D_i^-T, E_i = D_i^-1 C_i and F_i = D_i^-T C_{i+1}^T.
+  int32_t bf_bw = 0;
+  int64_t bf_nblk = 0;
+  std::vector<double> bf;
 };
 
 gb_status validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
@@ -35,6 +37,6 @@ gb_status validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
 gb_status build_host_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h,
                          const double* s, HostBSR* out);
 void preconditioned_s_bounds(HostBSR* hb);
-void band_cholesky(HostBSR* hb);
+void block_factor(HostBSR* hb);
 
 }  // namespace gb

@@ -55,10 +55,12 @@ struct DevMat {
   const double* h_val;
   const double* s_val;
   double s_lam_min, s_lam_max;  // spectrum bounds of the block-Jacobi-preconditioned S
-  int chol_bw;  // half-bandwidth of the banded Cholesky factor of S (0: none)
-  const float* chol_up;    // [4 nb][64] L(i+1+t, i)
-  const float* chol_row;   // [4 nb][64] L(i, i-1-t)
-  const float* chol_invd;  // [4 nb] 1 / L(i, i)
+  // Block-bidiagonal Cholesky factor of S on 64-row blocks (bf_bw = 0: none):
+  // four [bf_nblk][64][64] arrays, k-major (entry (r, k) at k * 64 + r):
+  // D_i^-1, D_i^-T, E_i = D_i^-1 C_i, F_i = D_i^-T C_{i+1}^T; FP32 and FP64.
+  int bf_bw, bf_nblk;
+  const float* bf32;
+  const double* bf64;
 };
 
 // ------------------------------------------------------------ complex FP64
@@ -78,7 +80,7 @@ __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isf
 
 // ------------------------------------------------------------ block reduce
 struct RedSmem {
-  double red[NWARP * NVMAX * 32];
+  double* red;  // NWARP * NVMAX * 32 partials at the start of the team's dynamic shared memory
   double scal[NVMAX * WMAX];
 };
 
@@ -162,6 +164,34 @@ __device__ __forceinline__ void bsr_row_f(const DevMat& m, const float* __restri
       acc[r].y = fmaf(a.z, xv[2].y, acc[r].y);
       acc[r].x = fmaf(a.w, xv[3].x, acc[r].x);
       acc[r].y = fmaf(a.w, xv[3].y, acc[r].y);
+    }
+  }
+}
+
+// FP32 matrix (hi part) times the hi parts of a float-float complex vector
+// (float4 {re.hi, re.lo, im.hi, im.lo}), FP32 accumulation: the unrefined
+// FP32 product (flags bit 5 of the mixed path).
+__device__ __forceinline__ void bsr_row_fhi(const DevMat& m, const float* __restrict__ A,
+                                            const float4* __restrict__ x, int W, int c, int I, float2 (&acc)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_float2(0.f, 0.f);
+  const int b1 = m.blk_ptr[I + 1];
+#pragma unroll kUnroll
+  for (int b = m.blk_ptr[I]; b < b1; ++b) {
+    const int J = m.blk_col[b];
+    const float4* xr = x + (size_t)(4 * J) * W + c;
+    float2 xv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float4 v = xr[(size_t)t * W];
+      xv[t] = make_float2(v.x, v.z);
+    }
+    const float4* ab = reinterpret_cast<const float4*>(A + (size_t)b * 16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 a = __ldg(ab + r);
+      acc[r].x = fmaf(a.x, xv[0].x, fmaf(a.y, xv[1].x, fmaf(a.z, xv[2].x, fmaf(a.w, xv[3].x, acc[r].x))));
+      acc[r].y = fmaf(a.x, xv[0].y, fmaf(a.y, xv[1].y, fmaf(a.z, xv[2].y, fmaf(a.w, xv[3].y, acc[r].y))));
     }
   }
 }

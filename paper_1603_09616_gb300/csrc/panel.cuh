@@ -34,6 +34,14 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 // r_m[R_j] for every column of the panel -> one history row (FP64).
 template <bool MIX>
 __device__ void gather_hist(const Args& a, const Smem& sm, const SeedT<MIX>* r, double2* row) {
+  if (a.full_hist) {  // every row of every column: row[cc * N4 + i]
+    const int N4 = 4 * a.m.nb, W = a.W;
+    for (int e = threadIdx.x; e < N4 * W; e += TPB) {
+      const int cc = e / N4, i = e - cc * N4;
+      row[e] = to_d2(r[(size_t)i * W + cc]);
+    }
+    return;
+  }
   const int M = sm.off[a.W];
   for (int e = threadIdx.x; e < M; e += TPB) {
     int cc = 0;
@@ -79,7 +87,7 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
   // inner-CG vectors: shared memory when the panel fits (g, d, q), else global
   using CgT = typename std::conditional<MIX, float2, double2>::type;
   CgT* cg_x = wsp<CgT>(ws, a.o_x);
-  CgT* cg_g = a.cg_smem ? reinterpret_cast<CgT*>(dyn) : wsp<CgT>(ws, a.o_g);
+  CgT* cg_g = a.cg_smem ? reinterpret_cast<CgT*>(dyn + dyn_layout(!MIX, W, false, 0).o_cg) : wsp<CgT>(ws, a.o_g);
   CgT* cg_d = a.cg_smem ? cg_g + NE : wsp<CgT>(ws, a.o_d);
   CgT* cg_q = a.cg_smem ? cg_d + NE : wsp<CgT>(ws, a.o_q);
 
@@ -128,9 +136,9 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 
   // r_0 = S^{-1} b
   if constexpr (MIX) {
-    inner_mixed(a, sm, rt, r, cg_x, cg_g, cg_d, cg_q);
+    inner_mixed(a, sm, rt, r, cg_x, cg_g, cg_d, cg_q, dyn);
   } else {
-    cg64(a, sm, rt, r, cg_g, cg_d, cg_q);
+    inner64(a, sm, rt, r, cg_g, cg_d, cg_q, dyn);
   }
   {  // p = r, Sp = rt, rho_0 = r^T rt
     double v[2] = {0, 0};
@@ -196,7 +204,17 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
           wbsr_row_ff(a.m, a.m.hb_hi, a.m.hb_lo, p, W, W, lane, I, act, are, aim);
           if (lane >= W || !act) continue;
 #else
-          bsr_row_ff(a.m, a.m.hb_hi, a.m.hb_lo, p, W, c, I, are, aim);
+          if (a.hp_fp32) {  // unrefined FP32 product: U = H hi(p), accumulated in FP32
+            float2 acc[4];
+            bsr_row_fhi(a.m, a.m.hb_hi, p, W, c, I, acc);
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+              are[rr] = gbff::acc{acc[rr].x, 0.f};
+              aim[rr] = gbff::acc{acc[rr].y, 0.f};
+            }
+          } else {
+            bsr_row_ff(a.m, a.m.hb_hi, a.m.hb_lo, p, W, c, I, are, aim);
+          }
 #endif
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
@@ -251,9 +269,9 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 
     // w = S^{-1} U
     if constexpr (MIX) {
-      inner_mixed(a, sm, U, w, cg_x, cg_g, cg_d, cg_q);
+      inner_mixed(a, sm, U, w, cg_x, cg_g, cg_d, cg_q, dyn);
     } else {
-      cg64(a, sm, U, w, cg_g, cg_d, cg_q);
+      inner64(a, sm, U, w, cg_g, cg_d, cg_q, dyn);
     }
 
     if (tid < W && sm.act[tid]) {
@@ -438,8 +456,8 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
 
   // ---------------------------------------------------------------- final phase
   const int KG = a.KG;
-  // F0: t_m = sum_{i in R_j} S_ji r_m[i]
-  {
+  // F0: t_m = sum_{i in R_j} S_ji r_m[i]  (not in verification mode: no LDOS)
+  if (!a.full_hist) {
     int nmax = 0;
     for (int i = 0; i < W; ++i) nmax = max(nmax, sm.nc[i]);
     for (int e = tid; e < (nmax + 1) * W; e += TPB) {
@@ -598,7 +616,7 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
     }
     if (a.iters) a.iters[col] = sm.nc[tid];
     if (a.inner_iters) a.inner_iters[col] = sm.inner_count;
-    int st = sm.st[tid];
+    int st = sm.st[tid] | (sm.bc_fail ? kStTimeout : 0);
     for (int k = 0; k < K; ++k)
       if (!(resk[tid * K + k] <= a.tol)) st |= kStNoConv;
     a.status[col] = st;
@@ -628,6 +646,13 @@ __global__ void __launch_bounds__(TPB, MIN_TEAMS_PER_SM) team_kernel(const __gri
   __shared__ PanelSmemExtra sx;
   extern __shared__ __align__(16) char dyn_smem[];
   char* ws = a.team_ws + (size_t)blockIdx.x * a.team_bytes;
+  team_init(sm, dyn_smem);
+  if (a.full_hist) {  // verification: one panel per team, panel = team
+    if (threadIdx.x == 0) sm.panel = blockIdx.x;
+    __syncthreads();
+    if (sm.panel < a.npanels) solve_panel<MIX>(a, sm, sx, ws, dyn_smem);
+    return;
+  }
   for (;;) {
     if (threadIdx.x == 0) sm.panel = atomicAdd(a.panel_counter, 1);
     __syncthreads();
@@ -653,6 +678,7 @@ __global__ void __launch_bounds__(TPB, MIN_TEAMS_PER_SM)
   __shared__ int s_sys;
   extern __shared__ __align__(16) char dyn_smem[];
   char* ws = team_ws + (size_t)blockIdx.x * team_bytes;
+  team_init(sm, dyn_smem);
   const int total = panel_prefix[nsys];
   for (;;) {
     if (threadIdx.x == 0) {

@@ -288,20 +288,17 @@ gb_status gb_bsr_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_i
   return GB_OK;
 }
 
-gb_status gb_band_cholesky_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
-                                   const double* s_val, int32_t* bw, float* up, float* row, float* invd) {
+gb_status gb_block_factor_to_host(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* h_val,
+                                  const double* s_val, int32_t* bw, int64_t* nblk, double* factor) {
   clear_error();
-  if (!bw) return fail(GB_EINVAL, "bw must not be NULL");
+  if (!bw || !nblk) return fail(GB_EINVAL, "bw and nblk must not be NULL");
   HostBSR hb;
   gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
   if (st != GB_OK) return st;
-  band_cholesky(&hb);
-  *bw = hb.chol_bw;
-  if (hb.chol_bw > 0) {
-    if (up) std::memcpy(up, hb.chol_up.data(), sizeof(float) * hb.chol_up.size());
-    if (row) std::memcpy(row, hb.chol_row.data(), sizeof(float) * hb.chol_row.size());
-    if (invd) std::memcpy(invd, hb.chol_invd.data(), sizeof(float) * hb.chol_invd.size());
-  }
+  block_factor(&hb);
+  *bw = hb.bf_bw;
+  *nblk = hb.bf_nblk;
+  if (factor && !hb.bf.empty()) std::memcpy(factor, hb.bf.data(), sizeof(double) * hb.bf.size());
   return GB_OK;
 }
 
@@ -314,7 +311,7 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   gb_status st = build_host_bsr(n, row_ptr, col_idx, h_val, s_val, &hb);
   if (st != GB_OK) return st;
   preconditioned_s_bounds(&hb);
-  band_cholesky(&hb);
+  block_factor(&hb);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
   GB_CUDA(cudaGetDevice(&dev));
@@ -334,9 +331,8 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   const size_t o_mi = take(sizeof(double) * nbl * 16), o_m32 = take(sizeof(float) * nbl * 16);
   const size_t o_rp = take(sizeof(int) * (n + 1)), o_ci = take(sizeof(int) * nnz);
   const size_t o_hv = take(sizeof(double) * nnz), o_sv = take(sizeof(double) * nnz);
-  const size_t nch = hb.chol_bw > 0 ? 4 * nbl : 0;
-  const size_t o_cu = take(sizeof(float) * nch * 64), o_cr = take(sizeof(float) * nch * 64);
-  const size_t o_cd = take(sizeof(float) * nch);
+  const size_t nbf = hb.bf.size();  // 4 x nblk x 4096 factor entries (0: no factor)
+  const size_t o_bf64 = take(sizeof(double) * nbf), o_bf32 = take(sizeof(float) * nbf);
   const size_t total = off;
 
   std::vector<char> host(total, 0);
@@ -369,10 +365,10 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   put(o_ci, hb.col_idx.data(), sizeof(int) * nnz);
   put(o_hv, hb.h_val.data(), sizeof(double) * nnz);
   put(o_sv, hb.s_val.data(), sizeof(double) * nnz);
-  if (nch) {
-    put(o_cu, hb.chol_up.data(), sizeof(float) * nch * 64);
-    put(o_cr, hb.chol_row.data(), sizeof(float) * nch * 64);
-    put(o_cd, hb.chol_invd.data(), sizeof(float) * nch);
+  if (nbf) {
+    put(o_bf64, hb.bf.data(), sizeof(double) * nbf);
+    float* f32 = reinterpret_cast<float*>(host.data() + o_bf32);
+    for (size_t i = 0; i < nbf; ++i) f32[i] = (float)hb.bf[i];
   }
 
   gb_matrix* m = new gb_matrix();
@@ -415,10 +411,10 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   d.s_val = reinterpret_cast<const double*>(b + o_sv);
   d.s_lam_min = hb.lam_min;
   d.s_lam_max = hb.lam_max;
-  d.chol_bw = nch ? hb.chol_bw : 0;
-  d.chol_up = nch ? reinterpret_cast<const float*>(b + o_cu) : nullptr;
-  d.chol_row = nch ? reinterpret_cast<const float*>(b + o_cr) : nullptr;
-  d.chol_invd = nch ? reinterpret_cast<const float*>(b + o_cd) : nullptr;
+  d.bf_bw = nbf ? hb.bf_bw : 0;
+  d.bf_nblk = nbf ? (int)hb.bf_nblk : 0;
+  d.bf64 = nbf ? reinterpret_cast<const double*>(b + o_bf64) : nullptr;
+  d.bf32 = nbf ? reinterpret_cast<const float*>(b + o_bf32) : nullptr;
   *out = m;
   return GB_OK;
 }
@@ -433,9 +429,10 @@ gb_status gb_matrix_get_info(const gb_matrix* m, gb_matrix_info* info) {
   info->max_row = m->max_row;
   info->block = 4;
   info->device = m->device;
-  info->reserved = 0;
+  info->factor_bw = m->dm.bf_bw;
   info->s_lam_min = m->dm.s_lam_min;
   info->s_lam_max = m->dm.s_lam_max;
+  info->factor_nblk = m->dm.bf_nblk;
   return GB_OK;
 }
 
@@ -462,8 +459,12 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
   void* pad = nullptr;
   if (n4 != m->n) {  // last block column reads rows up to 4*nb - 1: pad x with zero rows
     GB_CUDA(cudaMallocAsync(&pad, esz * n4 * w, s));
-    GB_CUDA(cudaMemsetAsync(pad, 0, esz * n4 * w, s));
-    GB_CUDA(cudaMemcpyAsync(pad, x, esz * m->n * w, cudaMemcpyDeviceToDevice, s));
+    cudaError_t pe = cudaMemsetAsync(pad, 0, esz * n4 * w, s);
+    if (pe == cudaSuccess) pe = cudaMemcpyAsync(pad, x, esz * m->n * w, cudaMemcpyDeviceToDevice, s);
+    if (pe != cudaSuccess) {  // free the padded copy on this exit path too
+      cudaFreeAsync(pad, s);
+      return cuda_fail(pe, "spmm input padding");
+    }
     xin = pad;
   }
   const int threads = 256;
@@ -500,19 +501,35 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
 // ------------------------------------------------------------ shifted solve
 namespace {
 
-// Inner solver of the mixed path: Chebyshev (default) when the spectrum bounds
-// of the preconditioned S are known and positive, CG when flags bit 2 asks for
-// it.  K steps reduce the preconditioned residual below itol by the Chebyshev
-// bound 2 sqrt(kappa) q^K (q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1)), with
-// the Lanczos bounds widened by 2% on each side.
+// Inner solver: the exact block-bidiagonal Cholesky solve when S's
+// half-bandwidth is at most 63 (both precisions), unless flags ask for an
+// iteration.  Otherwise the mixed path runs Chebyshev when the spectrum bounds
+// of the preconditioned S are known and positive (CG with flags bit 2), and
+// the FP64 path runs CG.  K Chebyshev steps reduce the preconditioned residual
+// below itol by the bound 2 sqrt(kappa) q^K (q = (sqrt(kappa) - 1) /
+// (sqrt(kappa) + 1)), with the Lanczos bounds widened by 2% on each side.
+constexpr int kFlagSmem = 2, kFlagCG = 4, kFlagCheb = 16, kFlagHpF32 = 32;
 void set_inner_method(const gb_matrix* m, const gb_solve_params* p, double itol, gbk::Args& a) {
   std::memset(&a, 0, sizeof a);
-  if (p->prec == GB_MIXED && (p->flags & 8) && m->dm.chol_bw > 0) {
-    a.inner_chol = 1;  // banded Cholesky triangular solves on both FP32 levels
+  a.hp_fp32 = (p->prec == GB_MIXED && (p->flags & kFlagHpF32)) ? 1 : 0;
+  if (!(p->flags & (kFlagCG | kFlagCheb)) && m->dm.bf_bw > 0) {
+    a.inner_bchol = 1;  // exact: block-bidiagonal Cholesky factor solves
+    // mixed: FP32 factor solves, each accurate to ~4e-7 (measured in an
+    // emulation of the kernel's arithmetic), refined around float-float
+    // residuals: two levels for tol >= 1e-7, three down to 1e-9, four below
+    // (measured: at tol 1e-10 a near-threshold pair of a 114-orbital chain
+    // stagnated at 7.7e-10 with three levels and converged with four); an
+    // explicit inner_tol asks for (4e-7)^levels <= inner_tol, two at least
+    if (p->inner_tol > 0) {
+      a.bc_levels = 2;
+      while (a.bc_levels < 4 && std::pow(4e-7, a.bc_levels) > p->inner_tol) ++a.bc_levels;
+    } else {
+      a.bc_levels = p->tol >= 1e-7 ? 2 : (p->tol >= 1e-9 ? 3 : 4);
+    }
     return;
   }
   const double lmin = m->dm.s_lam_min * 0.98, lmax = m->dm.s_lam_max * 1.02;
-  if (p->prec != GB_MIXED || (p->flags & 4) || !(lmin > 0.0) || !(lmax > lmin)) return;
+  if (p->prec != GB_MIXED || (p->flags & kFlagCG) || !(lmin > 0.0) || !(lmax > lmin)) return;
   const double kappa = lmax / lmin, sk = std::sqrt(kappa);
   const double q = (sk - 1.0) / (sk + 1.0);
   int K = (int)std::ceil(std::log(2.0 * sk / itol) / std::log(1.0 / q));
@@ -539,7 +556,7 @@ struct Plan {
   gbk::Args a;
 };
 
-gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, Plan* pl) {
+gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, Plan* pl, bool full_hist = false) {
   if (!m) return fail(GB_EINVAL, "matrix is NULL");
   if (!p) return fail(GB_EINVAL, "params is NULL");
   if (p->nshift < 1 || p->nshift > 256) return fail(GB_EINVAL, "nshift must be in [1, 256]");
@@ -573,8 +590,15 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   const size_t n4 = 4 * (size_t)m->nb;
   const size_t cg_esz = p->prec == GB_FP64 ? 16 : 8;
   const size_t smem_budget = (size_t)prop.sharedMemPerBlockOptin - 40 * 1024;
-  const bool want_smem = (p->flags & 2) != 0;
-  auto fits = [&](int w) { return want_smem && 3 * n4 * (size_t)w * cg_esz <= smem_budget; };
+  // the exact factor solve keeps its partial sums, its current block and (FP32)
+  // two staged factor tiles in dynamic shared memory instead
+  const bool bchol = !(p->flags & (kFlagCG | kFlagCheb)) && m->dm.bf_bw > 0;
+  const bool want_smem = (p->flags & kFlagSmem) != 0 && !bchol;
+  auto fits = [&](int w) { return want_smem && 3 * n4 * (size_t)w * cg_esz + gbk::kRedBytes <= smem_budget; };
+  auto dyn_bytes = [&](int w) -> size_t {
+    const unsigned cg = fits(w) ? (unsigned)(3 * n4 * (size_t)w * cg_esz) : 0u;
+    return gbk::dyn_layout(p->prec == GB_FP64, w, bchol, cg).bytes;
+  };
   auto occupancy = [&](size_t dyn) {
     int per_sm = 1;
     const void* fn = p->prec == GB_FP64 ? (const void*)gbk::team_kernel<false> : (const void*)gbk::team_kernel<true>;
@@ -589,7 +613,7 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
     // slots, ~20% faster than W = 4)
     W = 1;
     for (int cand : {32, 16, 8, 4, 2}) {
-      const size_t dyn = fits(cand) ? 3 * n4 * (size_t)cand * cg_esz : 0;
+      const size_t dyn = dyn_bytes(cand);
       if (4LL * ((p->nrhs + cand - 1) / cand) >= 3LL * nsm * occupancy(dyn)) {
         W = cand;
         break;
@@ -600,12 +624,12 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
     return fail(GB_EINVAL, "panel must be 1, 2, 4, 8, 16 or 32");
   pl->W = W;
   pl->cg_smem = fits(W) ? 1 : 0;
-  pl->dyn_smem = pl->cg_smem ? 3 * n4 * (size_t)W * cg_esz : 0;
+  pl->dyn_smem = dyn_bytes(W);
   pl->teams_per_sm = occupancy(pl->dyn_smem);
   pl->KG = (p->nshift + 31) / 32;
   pl->npanels = (p->nrhs + W - 1) / W;
   pl->teams = std::min(pl->npanels, nsm * pl->teams_per_sm);
-  pl->Mcap = W * m->max_row;
+  pl->Mcap = full_hist ? W * 4 * (int)m->nb : W * m->max_row;
   pl->inner_maxit = 500;
   // Inner-solve accuracy: the seed recurrence treats w = S^{-1} H p as exact,
   // and each iteration's error enters the shifted residual gap, so the inner
@@ -677,6 +701,8 @@ gb_status gb_solve_plan(const gb_matrix* m, const gb_solve_params* p, int32_t* p
   plan[1] = pl.teams;
   plan[2] = pl.cg_smem;
   plan[3] = (int32_t)pl.dyn_smem;
+  plan[4] = pl.a.inner_bchol ? 2 : (pl.a.inner_cheb ? 1 : 0);
+  plan[5] = pl.teams_per_sm;
   return GB_OK;
 }
 
@@ -781,6 +807,7 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
   GB_CUDA(cudaStreamSynchronize(s));
   int any = 0;
   for (int v : hst) any |= v;
+  if (any & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
   if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
   if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
   if (any & (gbk::kStNoConv | gbk::kStInner))
@@ -791,13 +818,382 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
 
 }  // extern "C"
 
+// ------------------------------------------------------------ standalone exact S^-1
+// One team applies the block-bidiagonal Cholesky solve to a panel of W
+// columns (the inner solve of the shifted recurrence, on its own: for tests
+// and for timing the factor solve).
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(gbk::TPB, 1)
+    sinv_kernel(const __grid_constant__ gbk::Args a, const typename gbk::CplxOf<T>::type* x,
+                typename gbk::CplxOf<T>::type* y, typename gbk::CplxOf<T>::type* t1,
+                typename gbk::CplxOf<T>::type* t2, int* status) {
+  __shared__ gbk::Smem sm;
+  extern __shared__ __align__(16) char dyn_smem[];
+  gbk::team_init(sm, dyn_smem);
+  if (threadIdx.x < gbk::WMAX) sm.act[threadIdx.x] = threadIdx.x < a.W ? 1 : 0;
+  if (threadIdx.x == 0) sm.inner_count = 0;
+  __syncthreads();
+  gbk::bc_solve<T>(a, sm, x, y, t1, t2, dyn_smem);
+  if (threadIdx.x == 0) *status = sm.bc_fail ? gbk::kStTimeout : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+gb_status gb_apply_sinv(const gb_matrix* m, gb_precision prec, int32_t w, const void* x, void* y, void* stream) {
+  clear_error();
+  if (!m || !x || !y) return fail(GB_EINVAL, "NULL argument");
+  if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32)
+    return fail(GB_EINVAL, "w must be 1, 2, 4, 8, 16 or 32");
+  if (prec != GB_FP64 && prec != GB_MIXED) return fail(GB_EINVAL, "bad precision");
+  if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device %d differs from the matrix's device %d", dev, m->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool f64 = prec == GB_FP64;
+  const size_t esz = f64 ? 16 : 8, n4 = 4 * (size_t)m->nb, panel = esz * n4 * w;
+  // padded input, output and two scratch panels, plus the status word
+  char* buf = nullptr;
+  GB_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&buf), 4 * panel + 256, s));
+  char* xin = buf;
+  char* yout = buf + panel;
+  int* st = reinterpret_cast<int*>(buf + 4 * panel);
+  cudaError_t e = cudaMemsetAsync(buf, 0, 4 * panel + 256, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xin, x, esz * m->n * w, cudaMemcpyDeviceToDevice, s);
+  gbk::Args a;
+  std::memset(&a, 0, sizeof a);
+  a.m = m->dm;
+  a.W = w;
+  a.inner_bchol = 1;
+  const size_t dyn = gbk::dyn_layout(f64, w, true, 0).bytes;
+  if (e == cudaSuccess) {
+    if (f64) {
+      e = cudaFuncSetAttribute(sinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e == cudaSuccess)
+        sinv_kernel<double><<<1, gbk::TPB, dyn, s>>>(a, reinterpret_cast<const double2*>(xin),
+                                                      reinterpret_cast<double2*>(yout),
+                                                      reinterpret_cast<double2*>(buf + 2 * panel),
+                                                      reinterpret_cast<double2*>(buf + 3 * panel), st);
+    } else {
+      e = cudaFuncSetAttribute(sinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e == cudaSuccess)
+        sinv_kernel<float><<<1, gbk::TPB, dyn, s>>>(a, reinterpret_cast<const float2*>(xin),
+                                                    reinterpret_cast<float2*>(yout),
+                                                    reinterpret_cast<float2*>(buf + 2 * panel),
+                                                    reinterpret_cast<float2*>(buf + 3 * panel), st);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  int hst = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(y, yout, esz * m->n * w, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gb_apply_sinv");
+  if (hst & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
+  return GB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ true-residual check
+// The recursive estimate ||rt_n|| / |pi^k_n| equals the true residual only
+// while every inner solve is exact; an inexact S^-1 makes them drift apart.
+// The check re-runs the listed columns in the same precision with the full
+// history r_m kept on every row, forms x^k = sum_m c^k_m r_m for every shift
+// (a complex GEMM of the history with the coefficients) and evaluates
+// ||e_j - (z_k S - H) x^k||_2 in FP64 from the scalar CSR.
+namespace {
+
+// X[v][i][k] = sum_{m < nk[k]} c[m][k] r_m[i] for verified column v (panel
+// v / W, slot v % W): 64 rows x 32 shifts per block, 16 history steps staged
+// in shared memory per round, each thread 4 rows x 2 shifts.
+__global__ void __launch_bounds__(256) xk_kernel(int N4, int K, int W, int Mcap, int nver, const char* team_ws,
+                                                 size_t team_bytes, size_t o_hr, size_t o_cg, size_t o_nk,
+                                                 const int* iters_max, double2* __restrict__ X) {
+  __shared__ double2 Rs[16][64];
+  __shared__ double2 Cs[16][32];
+  const int v = blockIdx.z, t = v / W, cc = v % W;
+  const int i0 = blockIdx.x * 64, k0 = blockIdx.y * 32;
+  const char* ws = team_ws + (size_t)t * team_bytes;
+  const double2* hr = reinterpret_cast<const double2*>(ws + o_hr);
+  const double2* cg = reinterpret_cast<const double2*>(ws + o_cg);
+  const int* nk = reinterpret_cast<const int*>(ws + o_nk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[4][2];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  const int M = iters_max[v];
+  for (int m0 = 0; m0 < M; m0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int mm = e >> 6, i = e & 63;
+      const int m = m0 + mm, row = i0 + i;
+      Rs[mm][i] = (m < M && row < N4) ? hr[(size_t)m * Mcap + (size_t)cc * N4 + row] : make_double2(0.0, 0.0);
+    }
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      const int mm = e >> 5, kk = e & 31;
+      const int m = m0 + mm, k = k0 + kk;
+      Cs[mm][kk] = (k < K && m < nk[cc * K + k]) ? cg[((size_t)m * W + cc) * K + k] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int mm = 0; mm < 16; ++mm) {
+      double2 r[4], c[2];
+      for (int a = 0; a < 4; ++a) r[a] = Rs[mm][ty * 4 + a];
+      for (int b = 0; b < 2; ++b) c[b] = Cs[mm][tx * 2 + b];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 2; ++b) {
+          acc[a][b].x = fma(r[a].x, c[b].x, fma(-r[a].y, c[b].y, acc[a][b].x));
+          acc[a][b].y = fma(r[a].x, c[b].y, fma(r[a].y, c[b].x, acc[a][b].y));
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int row = i0 + ty * 4 + a, k = k0 + tx * 2 + b;
+      if (row < N4 && k < K) X[((size_t)v * N4 + row) * K + k] = acc[a][b];
+    }
+}
+
+// res[k][v] = || e_j - (z_k S - H) x^k ||_2 from the scalar CSR, FP64; one
+// block per (column, 32 shifts), lane = shift, warps split the rows, fixed
+// reduction order.
+__global__ void __launch_bounds__(256) true_resid_kernel(const gbk::DevMat mt, int N4, int K, int nver,
+                                                         const int* __restrict__ cols, const double2* __restrict__ z,
+                                                         const double2* __restrict__ X, double* __restrict__ res) {
+  __shared__ double part[8][32];
+  const int v = blockIdx.x, k = blockIdx.y * 32 + (threadIdx.x & 31), warp = threadIdx.x >> 5;
+  const int j = cols[v];
+  double acc = 0.0;
+  if (k < K) {
+    const double2 zk = z[k];
+    const double2* Xv = X + (size_t)v * N4 * K;
+    for (int i = warp; i < mt.n; i += 8) {
+      double2 sx = make_double2(0.0, 0.0), hx = make_double2(0.0, 0.0);
+      for (int t = mt.row_ptr[i]; t < mt.row_ptr[i + 1]; ++t) {
+        const double2 xv = Xv[(size_t)mt.col_idx[t] * K + k];
+        const double sv = mt.s_val[t], hv = mt.h_val[t];
+        sx.x = fma(sv, xv.x, sx.x);
+        sx.y = fma(sv, xv.y, sx.y);
+        hx.x = fma(hv, xv.x, hx.x);
+        hx.y = fma(hv, xv.y, hx.y);
+      }
+      // r_i = delta_ij - z_k (S x)_i + (H x)_i
+      double rr = (i == j ? 1.0 : 0.0) - (zk.x * sx.x - zk.y * sx.y) + hx.x;
+      double ri = -(zk.x * sx.y + zk.y * sx.x) + hx.y;
+      acc = fma(rr, rr, fma(ri, ri, acc));
+    }
+  }
+  part[warp][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (warp == 0 && k < K) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += part[w][threadIdx.x];
+    res[(size_t)k * nver + v] = sqrt(s);
+  }
+}
+
+struct VerLayout {
+  Plan pl;
+  int W;
+  size_t o_x, o_im, o_cols, total;
+};
+
+gb_status ver_layout(const gb_matrix* m, const gb_solve_params* p, int32_t nver, VerLayout* L,
+                     std::vector<int32_t>* cols_out, const int32_t* ver) {
+  if (nver < 1 || nver > 1024) return fail(GB_EINVAL, "nver must be in [1, 1024]");
+  gb_solve_params q = *p;
+  std::vector<int32_t> cols(nver, 0);
+  if (ver) {
+    for (int i = 0; i < nver; ++i) {
+      if (ver[i] < 0 || ver[i] >= p->nrhs) return fail(GB_EINVAL, "verify index %d out of range", i);
+      cols[i] = p->rhs_cols[ver[i]];
+    }
+  } else {
+    for (int i = 0; i < nver; ++i) cols[i] = p->rhs_cols[0];
+  }
+  int W = 1;
+  while (W < 8 && W < nver) W <<= 1;
+  q.nrhs = nver;
+  q.rhs_cols = cols.data();
+  q.panel = W;
+  gb_status st = make_plan(m, &q, true, &L->pl, true);
+  if (st != GB_OK) return st;
+  L->W = W;
+  L->pl.teams = L->pl.npanels;  // verification: every panel at once, one team each
+  size_t off = align256(L->pl.header_bytes) + L->pl.team_bytes * L->pl.teams;
+  off = align256(off);
+  L->o_x = off;
+  off = align256(off + (size_t)nver * 4 * m->nb * p->nshift * 16);
+  L->o_im = off;
+  off = align256(off + sizeof(int) * nver);
+  L->o_cols = off;
+  off = align256(off + sizeof(int) * nver);
+  L->total = off + 256;
+  if (cols_out) *cols_out = cols;
+  return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_true_residual_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t nver) {
+  clear_error();
+  if (!m || !p) {
+    fail(GB_EINVAL, "NULL argument");
+    return 0;
+  }
+  VerLayout L;
+  if (ver_layout(m, p, nver, &L, nullptr, nullptr) != GB_OK) return 0;
+  return L.total;
+}
+
+gb_status gb_true_residual(const gb_matrix* m, const gb_solve_params* p, int32_t nver, const int32_t* ver,
+                           double* resid_true, const gb_outputs* out, void* workspace, size_t workspace_bytes,
+                           void* stream, int32_t* nflagged) {
+  clear_error();
+  if (nflagged) *nflagged = 0;
+  if (!m || !p || !ver || !resid_true) return fail(GB_EINVAL, "NULL argument");
+  {
+    Plan full;  // validates the parameters of the solve being checked
+    const gb_status st = make_plan(m, p, false, &full);
+    if (st != GB_OK) return st;
+  }
+  if (out && (!out->resid || !out->col_status))
+    return fail(GB_EINVAL, "updating outputs needs their resid and col_status arrays");
+  VerLayout L;
+  std::vector<int32_t> cols;
+  gb_status st = ver_layout(m, p, nver, &L, &cols, ver);
+  if (st != GB_OK) return st;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < L.total)
+    return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device %d differs from the matrix's device %d", dev, m->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int K = p->nshift, N4 = 4 * (int)m->nb;
+  const Plan& pl = L.pl;
+  char* wsb = static_cast<char*>(workspace);
+  // header: shifts (no weights), columns, offsets, status, counter
+  std::vector<char> hdr(pl.header_bytes, 0);
+  double2* hz = reinterpret_cast<double2*>(hdr.data() + pl.o_z);
+  for (int k = 0; k < K; ++k) hz[k] = make_double2(p->z_re[k], p->z_im[k]);
+  std::memcpy(hdr.data() + pl.o_cols, cols.data(), sizeof(int) * nver);
+  long long* ho = reinterpret_cast<long long*>(hdr.data() + pl.o_off);
+  ho[0] = 0;
+  for (int i = 0; i < nver; ++i) ho[i + 1] = ho[i] + (m->h_row_ptr[cols[i] + 1] - m->h_row_ptr[cols[i]]);
+  GB_CUDA(cudaMemcpyAsync(wsb, hdr.data(), pl.header_bytes, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(wsb + L.o_cols, cols.data(), sizeof(int) * nver, cudaMemcpyHostToDevice, s));
+  gbk::Args a = pl.a;
+  a.m = m->dm;
+  a.K = K;
+  a.W = pl.W;
+  a.KG = pl.KG;
+  a.nrhs = nver;
+  a.npanels = pl.npanels;
+  a.maxit = p->maxit;
+  a.inner_maxit = pl.inner_maxit;
+  a.has_rho = 0;
+  a.has_edm = 0;
+  a.want_g = 1;
+  a.full_hist = 1;
+  a.tol = p->tol;
+  a.itol = pl.itol;
+  const int seed = p->seed_shift >= 0 ? p->seed_shift : K / 2;
+  a.sigma = make_double2(p->z_re[seed], p->z_im[seed]);
+  a.z = reinterpret_cast<const double2*>(wsb + pl.o_z);
+  a.w_rho = reinterpret_cast<const double2*>(wsb + pl.o_wr);
+  a.w_edm = reinterpret_cast<const double2*>(wsb + pl.o_we);
+  a.rhs_cols = reinterpret_cast<const int*>(wsb + pl.o_cols);
+  a.out_off = reinterpret_cast<const long long*>(wsb + pl.o_off);
+  a.status = reinterpret_cast<int*>(wsb + pl.o_status);
+  a.panel_counter = reinterpret_cast<int*>(wsb + pl.o_counter);
+  a.team_ws = wsb + align256(pl.header_bytes);
+  a.team_bytes = pl.team_bytes;
+  a.Mcap = pl.Mcap;
+  a.iters = reinterpret_cast<int*>(wsb + L.o_im);
+  a.cg_smem = pl.cg_smem;
+  if (p->prec == GB_FP64) {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<false><<<pl.teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  } else {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pl.dyn_smem));
+    gbk::team_kernel<true><<<pl.teams, gbk::TPB, pl.dyn_smem, s>>>(a);
+  }
+  GB_CUDA(cudaGetLastError());
+  double2* X = reinterpret_cast<double2*>(wsb + L.o_x);
+  {
+    const dim3 grid((unsigned)((N4 + 63) / 64), (unsigned)((K + 31) / 32), (unsigned)nver);
+    xk_kernel<<<grid, 256, 0, s>>>(N4, K, pl.W, pl.Mcap, nver, a.team_ws, pl.team_bytes, a.o_hr, a.o_cg, a.o_nk,
+                                   a.iters, X);
+    GB_CUDA(cudaGetLastError());
+  }
+  {
+    const dim3 grid((unsigned)nver, (unsigned)((K + 31) / 32));
+    true_resid_kernel<<<grid, 256, 0, s>>>(m->dm, N4, K, nver, reinterpret_cast<const int*>(wsb + L.o_cols), a.z, X,
+                                           resid_true);
+    GB_CUDA(cudaGetLastError());
+  }
+  std::vector<int> vst(nver);
+  GB_CUDA(cudaMemcpyAsync(vst.data(), a.status, sizeof(int) * nver, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  int any = 0;
+  for (int v : vst) any |= v;
+  if (any & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
+  if (out) {  // columns whose true residual misses tol become unconverged in `out`
+    const int nrhs = p->nrhs;
+    std::vector<double> rt((size_t)K * nver);
+    GB_CUDA(cudaMemcpyAsync(rt.data(), resid_true, sizeof(double) * K * nver, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> cst(nrhs);
+    GB_CUDA(cudaMemcpyAsync(cst.data(), out->col_status, sizeof(int32_t) * nrhs, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    int flagged = 0;
+    for (int v = 0; v < nver; ++v) {
+      const int c = ver[v];
+      bool miss = false;
+      for (int k = 0; k < K; ++k) miss |= !(rt[(size_t)k * nver + v] <= p->tol);
+      if (!miss) continue;
+      ++flagged;
+      cst[c] |= gbk::kStNoConv;
+      for (int k = 0; k < K; ++k) {
+        const double r = rt[(size_t)k * nver + v];
+        GB_CUDA(cudaMemcpyAsync(out->resid + (size_t)k * nrhs + c, &rt[(size_t)k * nver + v], sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+        if (out->converged) {
+          static const uint8_t zero = 0, one = 1;
+          GB_CUDA(cudaMemcpyAsync(out->converged + (size_t)k * nrhs + c, r <= p->tol ? &one : &zero, 1,
+                                  cudaMemcpyHostToDevice, s));
+        }
+      }
+      GB_CUDA(cudaMemcpyAsync(out->col_status + c, &cst[c], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (nflagged) *nflagged = flagged;
+  }
+  return GB_OK;
+}
+
+}  // extern "C"
+
 // ------------------------------------------------------------ correction solve
 // Shifted COCG with one seed can stagnate for a shift whose shifted residual
 // loses attainable accuracy (observed near the gap of some PPV-like chains at
-// eta = 0.02, in the mixed path and once in FP64).  The correction re-solves
-// each such column alone in plain FP64 with its worst unconverged shift as the
-// seed, so that shift's residual is the seed's own, and copies the column's
-// results over the first solve's.
+// eta = 0.02).  The correction re-solves each such column alone in plain FP64
+// (exact factor inner solve) with its worst unconverged shift as the seed, so
+// that shift's residual is the seed's own.  If shifts still miss tol, it
+// repeats with the worst remaining shift as the next seed (up to six seeds)
+// and keeps, per shift, the result of the seed that served it best; the
+// column's outputs are then formed from those G_ij(z_k).
 namespace {
 
 struct CorrLayout {
@@ -819,7 +1215,8 @@ gb_status corr_layout(const gb_matrix* m, const gb_solve_params* p, bool want_g,
   q.flags = 0;
   q.inner_tol = 0.0;
   Plan pl;
-  const gb_status st = make_plan(m, &q, want_g, &pl);
+  (void)want_g;
+  const gb_status st = make_plan(m, &q, true, &pl);
   if (st != GB_OK) return st;
   const size_t K = p->nshift, mr = (size_t)std::max(m->max_row, 1);
   size_t off = align256(pl.total);
@@ -837,7 +1234,7 @@ gb_status corr_layout(const gb_matrix* m, const gb_solve_params* p, bool want_g,
   L->o_it = take(4);
   L->o_conv = take(K);
   L->o_res = take(K * 8);
-  L->o_g = want_g ? take(K * mr * 16) : 0;
+  L->o_g = take(K * mr * 16);  // always: the per-shift merge over seeds needs G on the pattern row
   L->o_in = take(4);
   L->o_st = take(4);
   L->total = off + 256;
@@ -897,68 +1294,155 @@ gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, c
   const long long P = off[nrhs];
   char* wsb = static_cast<char*>(workspace);
   int fixed = 0, left = 0;
+  constexpr int kMaxSeeds = 6;
   for (int c = 0; c < nrhs; ++c) {
     const int sc = hst[c];
     if (!(sc & gbk::kStNoConv) || (sc & (gbk::kStBreakdown | gbk::kStNotSPD))) continue;
-    int kw = -1;  // the column's worst unconverged shift becomes the seed
-    double rw = -1.0;
+    const int32_t col = p->rhs_cols[c];
+    const long long mc = off[c + 1] - off[c];
+    // per shift, the best FP64 result over the seeds tried so far
+    std::vector<double> best(K, INFINITY), tres(K);
+    std::vector<double2> bestg((size_t)K * mc), tg((size_t)K * mc);
+    std::vector<double> cur(K);  // residuals that pick the next seed
     for (int k = 0; k < K; ++k) {
       const size_t e = (size_t)k * nrhs + c;
       const bool conv = out->converged ? hconv[e] != 0 : hres[e] <= p->tol;
-      if (!conv && hres[e] > rw) {
-        rw = hres[e];
-        kw = k;
-      }
+      cur[k] = conv ? 0.0 : hres[e];
     }
-    if (kw < 0) kw = K / 2;
-    gb_solve_params q = *p;
-    const int32_t col = p->rhs_cols[c];
-    q.nrhs = 1;
-    q.rhs_cols = &col;
-    q.prec = GB_FP64;
-    q.seed_shift = kw;
-    q.panel = 1;
-    q.flags = 0;
-    q.inner_tol = 0.0;
-    gb_outputs t{};
-    t.ldos = out->ldos ? reinterpret_cast<double*>(wsb + L.o_ldos) : nullptr;
-    t.rho = out->rho ? reinterpret_cast<double*>(wsb + L.o_rho) : nullptr;
-    t.edm = out->edm ? reinterpret_cast<double*>(wsb + L.o_edm) : nullptr;
-    t.q = out->q ? reinterpret_cast<double*>(wsb + L.o_q) : nullptr;
-    t.e_loc = out->e_loc ? reinterpret_cast<double*>(wsb + L.o_e) : nullptr;
-    t.iters = out->iters ? reinterpret_cast<int32_t*>(wsb + L.o_it) : nullptr;
-    t.converged = out->converged ? reinterpret_cast<uint8_t*>(wsb + L.o_conv) : nullptr;
-    t.resid = reinterpret_cast<double*>(wsb + L.o_res);
-    t.g_proj = want_g ? reinterpret_cast<double*>(wsb + L.o_g) : nullptr;
-    t.inner_iters = out->inner_iters ? reinterpret_cast<int32_t*>(wsb + L.o_in) : nullptr;
-    t.col_status = reinterpret_cast<int32_t*>(wsb + L.o_st);
-    const gb_status sub = gb_shifted_solve(m, &q, &t, workspace, L.plan_total, stream);
-    if (sub != GB_OK && sub != GB_ENOCONV) return sub;
-    // copy column c of the single-column results into the first solve's outputs
-    const long long mc = off[c + 1] - off[c];
-    auto column = [&](void* dst, const void* src, size_t esz) {  // [K][nrhs] column c <- [K][1]
-      return cudaMemcpy2DAsync(static_cast<char*>(dst) + esz * c, esz * nrhs, src, esz, esz, K,
-                               cudaMemcpyDeviceToDevice, s);
-    };
-    auto one = [&](void* dst, const void* src, size_t esz) {
-      return cudaMemcpyAsync(static_cast<char*>(dst) + esz * c, src, esz, cudaMemcpyDeviceToDevice, s);
-    };
-    if (out->ldos) GB_CUDA(column(out->ldos, t.ldos, sizeof(double)));
-    if (out->converged) GB_CUDA(column(out->converged, t.converged, 1));
-    GB_CUDA(column(out->resid, t.resid, sizeof(double)));
-    if (out->rho) GB_CUDA(cudaMemcpyAsync(out->rho + off[c], t.rho, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
-    if (out->edm) GB_CUDA(cudaMemcpyAsync(out->edm + off[c], t.edm, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
-    if (out->q) GB_CUDA(one(out->q, t.q, sizeof(double)));
-    if (out->e_loc) GB_CUDA(one(out->e_loc, t.e_loc, sizeof(double)));
-    if (out->iters) GB_CUDA(one(out->iters, t.iters, sizeof(int32_t)));
-    if (out->inner_iters) GB_CUDA(one(out->inner_iters, t.inner_iters, sizeof(int32_t)));
-    GB_CUDA(one(out->col_status, t.col_status, sizeof(int32_t)));
-    if (want_g)
-      GB_CUDA(cudaMemcpy2DAsync(out->g_proj + 2 * off[c], 16 * (size_t)P, t.g_proj, 16 * (size_t)mc, 16 * (size_t)mc,
-                                K, cudaMemcpyDeviceToDevice, s));
-    // the next column's solve reuses the temporaries: gb_shifted_solve is
-    // stream-ordered after these copies
-    if (sub == GB_OK)
+    int it_sum = 0, in_sum = 0, rounds = 0;
+    bool done = false;
+    for (int round = 0; round < kMaxSeeds && !done; ++round) {
+      int kw = -1;  // the worst shift still missing tol becomes the seed
+      double rw = -1.0;
+      for (int k = 0; k < K; ++k)
+        if (cur[k] > p->tol && cur[k] > rw) {
+          rw = cur[k];
+          kw = k;
+        }
+      if (kw < 0) kw = K / 2;
+      gb_solve_params q = *p;
+      q.nrhs = 1;
+      q.rhs_cols = &col;
+      q.prec = GB_FP64;
+      q.seed_shift = kw;
+      q.panel = 1;
+      q.flags = 0;
+      q.inner_tol = 0.0;
+      gb_outputs t{};
+      t.ldos = out->ldos ? reinterpret_cast<double*>(wsb + L.o_ldos) : nullptr;
+      t.rho = out->rho ? reinterpret_cast<double*>(wsb + L.o_rho) : nullptr;
+      t.edm = out->edm ? reinterpret_cast<double*>(wsb + L.o_edm) : nullptr;
+      t.q = out->q ? reinterpret_cast<double*>(wsb + L.o_q) : nullptr;
+      t.e_loc = out->e_loc ? reinterpret_cast<double*>(wsb + L.o_e) : nullptr;
+      t.iters = reinterpret_cast<int32_t*>(wsb + L.o_it);
+      t.converged = out->converged ? reinterpret_cast<uint8_t*>(wsb + L.o_conv) : nullptr;
+      t.resid = reinterpret_cast<double*>(wsb + L.o_res);
+      t.g_proj = reinterpret_cast<double*>(wsb + L.o_g);
+      t.inner_iters = reinterpret_cast<int32_t*>(wsb + L.o_in);
+      t.col_status = reinterpret_cast<int32_t*>(wsb + L.o_st);
+      const gb_status sub = gb_shifted_solve(m, &q, &t, workspace, L.plan_total, stream);
+      if (sub != GB_OK && sub != GB_ENOCONV) return sub;
+      int hit = 0, hin = 0;
+      GB_CUDA(cudaMemcpyAsync(tres.data(), t.resid, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaMemcpyAsync(tg.data(), t.g_proj, sizeof(double2) * K * mc, cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaMemcpyAsync(&hit, t.iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaMemcpyAsync(&hin, t.inner_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaStreamSynchronize(s));
+      it_sum += hit;
+      in_sum += hin;
+      ++rounds;
+      if (round == 0 && sub == GB_OK) {
+        // one seed converged every shift: the solve's own outputs are the column's
+        auto column = [&](void* dst, const void* src, size_t esz) {  // [K][nrhs] column c <- [K][1]
+          return cudaMemcpy2DAsync(static_cast<char*>(dst) + esz * c, esz * nrhs, src, esz, esz, K,
+                                   cudaMemcpyDeviceToDevice, s);
+        };
+        auto one = [&](void* dst, const void* src, size_t esz) {
+          return cudaMemcpyAsync(static_cast<char*>(dst) + esz * c, src, esz, cudaMemcpyDeviceToDevice, s);
+        };
+        if (out->ldos) GB_CUDA(column(out->ldos, t.ldos, sizeof(double)));
+        if (out->converged) GB_CUDA(column(out->converged, t.converged, 1));
+        GB_CUDA(column(out->resid, t.resid, sizeof(double)));
+        if (out->rho) GB_CUDA(cudaMemcpyAsync(out->rho + off[c], t.rho, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
+        if (out->edm) GB_CUDA(cudaMemcpyAsync(out->edm + off[c], t.edm, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
+        if (out->q) GB_CUDA(one(out->q, t.q, sizeof(double)));
+        if (out->e_loc) GB_CUDA(one(out->e_loc, t.e_loc, sizeof(double)));
+        if (out->iters) GB_CUDA(one(out->iters, t.iters, sizeof(int32_t)));
+        if (out->inner_iters) GB_CUDA(one(out->inner_iters, t.inner_iters, sizeof(int32_t)));
+        GB_CUDA(one(out->col_status, t.col_status, sizeof(int32_t)));
+        if (want_g)
+          GB_CUDA(cudaMemcpy2DAsync(out->g_proj + 2 * off[c], 16 * (size_t)P, t.g_proj, 16 * (size_t)mc,
+                                    16 * (size_t)mc, K, cudaMemcpyDeviceToDevice, s));
+        // the next column's solve reuses the temporaries: stream-ordered after these copies
+        GB_CUDA(cudaStreamSynchronize(s));
+        done = true;
+        break;
+      }
+      bool all = true;
+      for (int k = 0; k < K; ++k) {
+        if (tres[k] < best[k]) {
+          best[k] = tres[k];
+          for (long long t2 = 0; t2 < mc; ++t2) bestg[(size_t)k * mc + t2] = tg[(size_t)k * mc + t2];
+        }
+        cur[k] = best[k];
+        all &= best[k] <= p->tol;
+      }
+      if (all) done = true;
+    }
+    if (rounds > 1 || !done) {
+      // Several seeds: every shift keeps the result of the seed that served it
+      // best, and the column's outputs are formed from those G_ij(z_k) on the
+      // pattern row (the same reductions as the solve's final phase).
+      std::vector<double> sv(mc), hv(mc);
+      const int base = (int)rp[col];
+      GB_CUDA(cudaMemcpyAsync(sv.data(), m->dm.s_val + base, sizeof(double) * mc, cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaMemcpyAsync(hv.data(), m->dm.h_val + base, sizeof(double) * mc, cudaMemcpyDeviceToHost, s));
+      GB_CUDA(cudaStreamSynchronize(s));
+      std::vector<double> ldos(K), rho(mc, 0.0), edm(mc, 0.0);
+      std::vector<uint8_t> conv(K);
+      for (int k = 0; k < K; ++k) {
+        double im = 0.0;
+        for (long long t2 = 0; t2 < mc; ++t2) im += bestg[(size_t)k * mc + t2].y * sv[t2];
+        ldos[k] = -im / 3.141592653589793238462643383279502884;
+        conv[k] = best[k] <= p->tol ? 1 : 0;
+        const double wr_re = p->w_rho ? p->w_rho[2 * k] : 0.0, wr_im = p->w_rho ? p->w_rho[2 * k + 1] : 0.0;
+        const double we_re = p->w_edm ? p->w_edm[2 * k] : 0.0, we_im = p->w_edm ? p->w_edm[2 * k + 1] : 0.0;
+        for (long long t2 = 0; t2 < mc; ++t2) {
+          const double2 g = bestg[(size_t)k * mc + t2];
+          rho[t2] += wr_re * g.y + wr_im * g.x;  // Im(c g)
+          edm[t2] += we_re * g.y + we_im * g.x;
+        }
+      }
+      double qs = 0.0, es = 0.0;
+      for (long long t2 = 0; t2 < mc; ++t2) {
+        qs += rho[t2] * sv[t2];
+        es += rho[t2] * hv[t2];
+      }
+      const bool allc = std::all_of(conv.begin(), conv.end(), [](uint8_t v) { return v != 0; });
+      const int32_t cst = allc ? 0 : gbk::kStNoConv;
+      done = allc;
+      for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nrhs + c;
+        if (out->ldos) GB_CUDA(cudaMemcpyAsync(out->ldos + e, &ldos[k], sizeof(double), cudaMemcpyHostToDevice, s));
+        if (out->converged) GB_CUDA(cudaMemcpyAsync(out->converged + e, &conv[k], 1, cudaMemcpyHostToDevice, s));
+        GB_CUDA(cudaMemcpyAsync(out->resid + e, &best[k], sizeof(double), cudaMemcpyHostToDevice, s));
+        if (want_g)
+          GB_CUDA(cudaMemcpyAsync(out->g_proj + 2 * ((size_t)k * P + off[c]), &bestg[(size_t)k * mc],
+                                  sizeof(double2) * mc, cudaMemcpyHostToDevice, s));
+      }
+      if (out->rho && p->w_rho)
+        GB_CUDA(cudaMemcpyAsync(out->rho + off[c], rho.data(), sizeof(double) * mc, cudaMemcpyHostToDevice, s));
+      if (out->edm && p->w_edm)
+        GB_CUDA(cudaMemcpyAsync(out->edm + off[c], edm.data(), sizeof(double) * mc, cudaMemcpyHostToDevice, s));
+      if (out->q && p->w_rho) GB_CUDA(cudaMemcpyAsync(out->q + c, &qs, sizeof(double), cudaMemcpyHostToDevice, s));
+      if (out->e_loc && p->w_rho) GB_CUDA(cudaMemcpyAsync(out->e_loc + c, &es, sizeof(double), cudaMemcpyHostToDevice, s));
+      if (out->iters) GB_CUDA(cudaMemcpyAsync(out->iters + c, &it_sum, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      if (out->inner_iters)
+        GB_CUDA(cudaMemcpyAsync(out->inner_iters + c, &in_sum, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      GB_CUDA(cudaMemcpyAsync(out->col_status + c, &cst, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      GB_CUDA(cudaStreamSynchronize(s));  // the host buffers above are this iteration's locals
+    }
+    if (done)
       ++fixed;
     else
       ++left;
@@ -1106,6 +1590,7 @@ gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, 
   GB_CUDA(cudaStreamSynchronize(s));
   int any = 0;
   for (int i = 0; i < nrhs; ++i) any |= g_static_status[i];
+  if (any & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
   if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
   if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
   if (any & (gbk::kStNoConv | gbk::kStInner))
@@ -1160,7 +1645,7 @@ size_t layout_team(size_t N4, int W, int K, int KG, int maxit, int Mcap, bool wa
 struct BatchPlan {
   int W, teams, total_panels, maxK, maxit, Mcap, KG;
   bool mixed, want_g;
-  size_t N4, team_bytes, header_bytes, total;
+  size_t N4, team_bytes, header_bytes, total, dyn_smem;
   std::vector<int> order;  // systems, largest estimated cost first
   gbk::Args proto;
 };
@@ -1197,16 +1682,23 @@ gb_status make_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_s
   const int nsm = prop.multiProcessorCount;
   const void* fn = prec == GB_FP64 ? (const void*)gbk::team_kernel_batched<false>
                                    : (const void*)gbk::team_kernel_batched<true>;
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gbk::TPB, 0) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  // dynamic shared memory: the factor solve's buffers (systems without a
+  // factor leave them unused)
+  auto dyn_bytes = [&](int w) -> size_t { return gbk::dyn_layout(prec == GB_FP64, w, true, 0).bytes; };
+  auto occupancy = [&](size_t dyn) {
+    int per_sm = 1;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gbk::TPB, dyn) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    return per_sm;
+  };
   int W = panel;
   if (W <= 0) {  // widest panel that still gives every resident team a work item
     W = 1;
     for (int cand : {32, 16, 8, 4, 2}) {
       long long np = 0;
       for (int s = 0; s < nsys; ++s) np += (params[s].nrhs + cand - 1) / cand;
-      if (4 * np >= 3LL * nsm * per_sm) {
+      if (4 * np >= 3LL * nsm * occupancy(dyn_bytes(cand))) {
         W = cand;
         break;
       }
@@ -1214,6 +1706,8 @@ gb_status make_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_s
   }
   if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32)
     return fail(GB_EINVAL, "panel must be 1, 2, 4, 8, 16 or 32");
+  bp->dyn_smem = dyn_bytes(W);
+  const int per_sm = occupancy(bp->dyn_smem);
   bp->W = W;
   bp->mixed = prec == GB_MIXED;
   bp->want_g = want_g;
@@ -1325,7 +1819,9 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
       gbk::Args im;
       set_inner_method(m, p, p->inner_tol > 0 ? p->inner_tol : (p->prec == GB_FP64 ? 1e-14 : 1e-7), im);
       a.inner_cheb = im.inner_cheb;
-      a.inner_chol = im.inner_chol;
+      a.inner_bchol = im.inner_bchol;
+      a.bc_levels = im.bc_levels;
+      a.hp_fp32 = im.hp_fp32;
       a.cheb_K = im.cheb_K;
       a.cheb_c0 = im.cheb_c0;
       std::memcpy(a.cheb_A, im.cheb_A, sizeof a.cheb_A);
@@ -1376,12 +1872,17 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
   const gbk::Args* d_desc = reinterpret_cast<const gbk::Args*>(wsb);
   const int* d_prefix = reinterpret_cast<const int*>(wsb + o_prefix);
   int* d_counter = reinterpret_cast<int*>(wsb + o_counter);
-  if (bp.mixed)
-    gbk::team_kernel_batched<true><<<bp.teams, gbk::TPB, 0, s>>>(d_desc, d_prefix, nsys, d_counter, team_ws,
-                                                                 bp.team_bytes);
-  else
-    gbk::team_kernel_batched<false><<<bp.teams, gbk::TPB, 0, s>>>(d_desc, d_prefix, nsys, d_counter, team_ws,
-                                                                  bp.team_bytes);
+  if (bp.mixed) {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bp.dyn_smem));
+    gbk::team_kernel_batched<true><<<bp.teams, gbk::TPB, bp.dyn_smem, s>>>(d_desc, d_prefix, nsys, d_counter,
+                                                                           team_ws, bp.team_bytes);
+  } else {
+    GB_CUDA(cudaFuncSetAttribute(gbk::team_kernel_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bp.dyn_smem));
+    gbk::team_kernel_batched<false><<<bp.teams, gbk::TPB, bp.dyn_smem, s>>>(d_desc, d_prefix, nsys, d_counter,
+                                                                            team_ws, bp.team_bytes);
+  }
   GB_CUDA(cudaGetLastError());
   GB_CUDA(cudaMemcpyAsync(hdr.data(), wsb, bp.header_bytes, cudaMemcpyDeviceToHost, s));
   GB_CUDA(cudaStreamSynchronize(s));
@@ -1390,6 +1891,7 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
     const int* hs = reinterpret_cast<const int*>(hdr.data() + o_status[q]);
     for (int i = 0; i < params[q].nrhs; ++i) any |= hs[i];
   }
+  if (any & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
   if (any & gbk::kStNotSPD) return fail(GB_ENOTSPD, "inner CG found S not positive definite");
   if (any & gbk::kStBreakdown) return fail(GB_EBREAKDOWN, "COCG breakdown in at least one column");
   if (any & (gbk::kStNoConv | gbk::kStInner))
@@ -1409,10 +1911,13 @@ gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, cons
   cudaEvent_t e0, e1;
   GB_CUDA(cudaEventCreate(&e0));
   GB_CUDA(cudaEventCreate(&e1));
-  const int cands[4] = {4, 8, 16, 32};
+  // the configuration's panel widths {8, 16, 32, 64} less 64: a 64-column
+  // panel's per-column shared state next to the factor solve's buffers would
+  // leave one team per SM instead of two
+  const int cands[3] = {8, 16, 32};
   float best = 1e30f;
   *best_panel = 0;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 3; ++i) {
     if (times_ms) times_ms[i] = -1.f;
     BatchPlan bp;
     if (make_batch_plan(nsys, mats, probe.data(), outs, cands[i], &bp) != GB_OK || bp.total > workspace_bytes)

@@ -59,7 +59,14 @@ struct Args {
   // Chebyshev inner iteration of the mixed path (inner_cheb = 1): K steps per
   // FP32 level with d_{k+1} = A_k d_k + B_k M^-1 r_{k+1}, d_0 = c0 M^-1 r_0.
   int inner_cheb, cheb_K;
-  int inner_chol;  // 1: the FP32 levels solve S x = r by the banded Cholesky factor
+  int inner_bchol;  // 1: S x = f by the block-bidiagonal Cholesky factor (exact; block_chol.cuh)
+  int bc_levels;    // mixed path: FP32 factor solves per application (refinement levels)
+  // Verification mode: team b solves panel b only and records r_m on every row
+  // (history row = W columns x N4 rows, column-major) instead of the pattern
+  // rows, for the true-residual check; only the coefficients (cgs), nk and
+  // the iteration counts are produced.
+  int full_hist;
+  int hp_fp32;  // mixed path: H p as an unrefined FP32 product (flags bit 5)
   float cheb_c0;
   float cheb_A[48], cheb_B[48];
   double* ldos;
@@ -80,6 +87,7 @@ constexpr int kStBreakdown = 1;
 constexpr int kStNotSPD = 2;
 constexpr int kStNoConv = 4;
 constexpr int kStInner = 8;
+constexpr int kStTimeout = 16;  // a bounded wait for a staged factor tile gave up
 
 struct Smem {
   RedSmem rs;
@@ -88,7 +96,31 @@ struct Smem {
   double2 rho[WMAX], alpha[WMAX], beta[WMAX], aprev[WMAX], bprev[WMAX], gam[WMAX];
   double rt2[WMAX], scl[WMAX];
   double cg_rho[2 * WMAX], cg_un[2 * WMAX], cg_gg[2 * WMAX], cg_a[2 * WMAX], cg_b[2 * WMAX];
+  unsigned long long bc_bar[3];  // mbarriers of the staged factor tiles (block_chol.cuh)
+  unsigned tile_base;            // factor tiles consumed so far in this launch
+  int bc_fail;                   // a bounded tile wait gave up
 };
+
+// Once per launch, before the team's first panel: the block-reduce scratch in
+// dynamic shared memory and the tile barriers of the block Cholesky solve.
+__device__ __forceinline__ void team_init(Smem& sm, char* dyn);
+
+}  // namespace gbk
+
+#include "block_chol.cuh"
+
+namespace gbk {
+
+__device__ __forceinline__ void team_init(Smem& sm, char* dyn) {
+  if (threadIdx.x == 0) {
+    sm.rs.red = reinterpret_cast<double*>(dyn);
+    for (int b = 0; b < kTileBufs; ++b) mbar_init(&sm.bc_bar[b], 1);
+    fence_mbar_init();
+    sm.tile_base = 0;
+    sm.bc_fail = 0;
+  }
+  __syncthreads();
+}
 
 template <typename T>
 __device__ __forceinline__ T* wsp(char* ws, size_t off) {
@@ -112,7 +144,7 @@ __device__ __noinline__ double2 pi_step(double2 cur, double2 prev, double2 a_n, 
 // Solves S x = f per real column (re, im parts separately), block-Jacobi
 // preconditioned, zero initial guess, until ||g|| <= itol ||f|| for every
 // active real column.
-__device__ void cg64(const Args& a, Smem& sm, const double2* __restrict__ f, double2* __restrict__ x,
+__device__ __noinline__ void cg64(const Args& a, Smem& sm, const double2* __restrict__ f, double2* __restrict__ x,
                      double2* __restrict__ g, double2* __restrict__ d, double2* __restrict__ q) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   {
@@ -267,7 +299,7 @@ __device__ void cg64(const Args& a, Smem& sm, const double2* __restrict__ f, dou
 // ------------------------------------------------------------ inner CG, FP32 loop
 // Runs on (x, g, d) already initialised (x = 0, g = rhs, d = M^-1 g) with
 // cg_rho / cg_un / cg_gg set.  FP32 vectors, FP64 scalars.
-__device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ g,
+__device__ __noinline__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ g,
                           float2* __restrict__ d, float2* __restrict__ q, double itol) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   const double it2 = itol * itol;
@@ -394,7 +426,7 @@ __device__ void cg32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float
 // Chebyshev semi-iteration on the block-Jacobi-preconditioned S (spectrum
 // bounds from gb_build_bsr) for x (= 0 on entry), r (= rhs), d_0 (= c0 M^-1 r)
 // already set: K fused steps, one barrier each, no reductions.
-__device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ r,
+__device__ __noinline__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, float2* __restrict__ r,
                             float2* __restrict__ dA, float2* __restrict__ dB) {
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   // x = sum_k d_k is updated every other step with two directions (d_k from
@@ -459,100 +491,6 @@ __device__ void cheb32_loop(const Args& a, Smem& sm, float2* __restrict__ x, flo
   }
 }
 
-// ------------------------------------------------------------ inner banded Cholesky, FP32
-// x = S^-1 r as L y = r, L^T x = y with the banded factor of gb_build_bsr, one
-// warp per column.  Column-oriented substitution: the partial sums of the rows
-// inside the band live in a 64-slot ring across the lanes (row k in slot
-// k mod 64, two slots per lane); each step finishes one row (its owner lane
-// scales by 1 / L(i,i), a shuffle broadcasts the value) and every other slot
-// subtracts its band entry times it, so a row costs one multiply, one
-// broadcast and one FMA on the critical path.  y is kept in the direction
-// vector d of the level (overwritten).
-__device__ void band_solve32(const Args& a, Smem& sm, const float2* __restrict__ r, float2* __restrict__ y,
-                             float2* __restrict__ x) {
-  const int W = a.W, N4 = 4 * a.m.nb, lane = threadIdx.x & 31;
-  const float* __restrict__ Lup = a.m.chol_up;
-  const float* __restrict__ Lrow = a.m.chol_row;
-  const float* __restrict__ invd = a.m.chol_invd;
-  const float2 zero = make_float2(0.f, 0.f);
-  for (int c = threadIdx.x >> 5; c < W; c += NWARP) {
-    if (!sm.act[c]) continue;
-    // forward: L y = r; the ring holds rows i .. i+63
-    float2 s0 = lane < N4 ? r[(size_t)lane * W + c] : zero;
-    float2 s1 = lane + 32 < N4 ? r[(size_t)(lane + 32) * W + c] : zero;
-    for (int i = 0; i < N4; ++i) {
-      const int so = i & 63;
-      const float2 own = (so >> 5) ? s1 : s0;
-      const float di = __ldg(invd + i);
-      float2 v = make_float2(own.x * di, own.y * di);
-      v.x = __shfl_sync(0xffffffffu, v.x, so & 31);
-      v.y = __shfl_sync(0xffffffffu, v.y, so & 31);
-      if (lane == 0) y[(size_t)i * W + c] = v;
-      const float* __restrict__ li = Lup + (size_t)i * 64;
-      {
-        const int slot = lane, t = (slot - i - 1) & 63;  // this slot holds row i + 1 + t
-        if (slot == so) {
-          s0 = i + 64 < N4 ? r[(size_t)(i + 64) * W + c] : zero;
-        } else {
-          const float l = __ldg(li + t);
-          s0.x = fmaf(-l, v.x, s0.x);
-          s0.y = fmaf(-l, v.y, s0.y);
-        }
-      }
-      {
-        const int slot = lane + 32, t = (slot - i - 1) & 63;
-        if (slot == so) {
-          s1 = i + 64 < N4 ? r[(size_t)(i + 64) * W + c] : zero;
-        } else {
-          const float l = __ldg(li + t);
-          s1.x = fmaf(-l, v.x, s1.x);
-          s1.y = fmaf(-l, v.y, s1.y);
-        }
-      }
-    }
-    __syncwarp();
-    // backward: L^T x = y; the ring holds rows i-63 .. i
-    {
-      const int base = N4 - 64;
-      const int ra = base + ((lane - base) & 63), rb = base + ((lane + 32 - base) & 63);
-      s0 = ra >= 0 ? y[(size_t)ra * W + c] : zero;
-      s1 = rb >= 0 ? y[(size_t)rb * W + c] : zero;
-    }
-    for (int i = N4 - 1; i >= 0; --i) {
-      const int so = i & 63;
-      const float2 own = (so >> 5) ? s1 : s0;
-      const float di = __ldg(invd + i);
-      float2 v = make_float2(own.x * di, own.y * di);
-      v.x = __shfl_sync(0xffffffffu, v.x, so & 31);
-      v.y = __shfl_sync(0xffffffffu, v.y, so & 31);
-      if (lane == 0) x[(size_t)i * W + c] = v;
-      const float* __restrict__ li = Lrow + (size_t)i * 64;
-      {
-        const int slot = lane, t = (i - 1 - slot) & 63;  // this slot holds row i - 1 - t
-        if (slot == so) {
-          s0 = i - 64 >= 0 ? y[(size_t)(i - 64) * W + c] : zero;
-        } else {
-          const float l = __ldg(li + t);
-          s0.x = fmaf(-l, v.x, s0.x);
-          s0.y = fmaf(-l, v.y, s0.y);
-        }
-      }
-      {
-        const int slot = lane + 32, t = (i - 1 - slot) & 63;
-        if (slot == so) {
-          s1 = i - 64 >= 0 ? y[(size_t)(i - 64) * W + c] : zero;
-        } else {
-          const float l = __ldg(li + t);
-          s1.x = fmaf(-l, v.x, s1.x);
-          s1.y = fmaf(-l, v.y, s1.y);
-        }
-      }
-    }
-  }
-  if (threadIdx.x == 0) ++sm.inner_count;
-  __syncthreads();
-}
-
 // Stores the per-real-column CG start scalars from a reduced {g^T z, ||f||^2}.
 __device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
   if (threadIdx.x < 2 * W) {
@@ -567,9 +505,17 @@ __device__ __forceinline__ void cg_start_scalars(Smem& sm, int W) {
 // ------------------------------------------------------------ inner solve, mixed
 // w = S^{-1} U to ~FP64 accuracy: FP32 CG on hi(U), a float-float residual
 // e = U - S x1, FP32 CG on e, w = x1 + x2 (float-float).
-__device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ U, float4* __restrict__ w,
+__device__ __noinline__ void inner_mixed_factor(const Args& a, Smem& sm, const float4* __restrict__ U, float4* __restrict__ w,
+                                   float2* __restrict__ x, float2* __restrict__ g, float2* __restrict__ d,
+                                   float2* __restrict__ q, char* dyn);
+
+__device__ __noinline__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ U, float4* __restrict__ w,
                             float2* __restrict__ x, float2* __restrict__ g, float2* __restrict__ d,
-                            float2* __restrict__ q) {
+                            float2* __restrict__ q, char* dyn) {
+  if (a.inner_bchol) {
+    inner_mixed_factor(a, sm, U, w, x, g, d, q, dyn);
+    return;
+  }
   const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
   const double itol = a.itol;
   {  // level 1 start: g = hi(U), d = M^-1 g, x = 0
@@ -604,9 +550,7 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     block_reduce<4>(v, W, sm.rs);
     cg_start_scalars(sm, W);
   }
-  if (a.inner_chol)
-    band_solve32(a, sm, g, d, x);
-  else if (a.inner_cheb)
+  if (a.inner_cheb)
     cheb32_loop(a, sm, x, g, d, q);
   else
     cg32_loop(a, sm, x, g, d, q, itol);
@@ -661,9 +605,7 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     }
     cg_start_scalars(sm, W);  // its barrier orders the x / w writes too
   }
-  if (a.inner_chol)
-    band_solve32(a, sm, g, d, x);
-  else if (a.inner_cheb)
+  if (a.inner_cheb)
     cheb32_loop(a, sm, x, g, d, q);
   else
     cg32_loop(a, sm, x, g, d, q, itol);
@@ -676,6 +618,87 @@ __device__ void inner_mixed(const Args& a, Smem& sm, const float4* __restrict__ 
     w[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
   __syncthreads();
+}
+
+// ------------------------------------------------------------ inner solve, mixed, exact factor
+// w = S^{-1} U to ~FP64 accuracy by refinement with FP32 factor solves:
+// x1 = S^-1 hi(U), w = x1; then per further level the float-float residual
+// e = U - S w and w += S^-1 e.  One FP32 solve is accurate to ~4e-7, so two
+// levels give ~1e-13 and three ~1e-19 (a.bc_levels, set from the tolerance).
+// g = U - S v (float-float) for the active columns; v is the FP32 vector x
+// (XV = float2) or the float-float w (XV = float4).  No barrier.
+template <typename XV>
+__device__ __noinline__ void ff_residual(const Args& a, const Smem& sm, const float4* __restrict__ U,
+                                         const XV* __restrict__ v, float2* __restrict__ g) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  for (int it = threadIdx.x; it < nb * W; it += TPB) {
+    if (!sm.act[c]) continue;
+    const int I = it / W;
+    gbff::acc are[4], aim[4];
+    if constexpr (sizeof(XV) == 8)
+      bsr_row_ffx(a.m, a.m.sb_hi, a.m.sb_lo, v, W, c, I, are, aim);
+    else
+      bsr_row_ff(a.m, a.m.sb_hi, a.m.sb_lo, v, W, c, I, are, aim);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const size_t e = (size_t)(4 * I + r) * W + c;
+      const float4 u = U[e];
+      const gbff::ff er = gbff::ff_sub(gbff::ff{u.x, u.y}, gbff::acc_get(are[r]));
+      const gbff::ff ei = gbff::ff_sub(gbff::ff{u.z, u.w}, gbff::acc_get(aim[r]));
+      g[e] = make_float2(er.hi + er.lo, ei.hi + ei.lo);
+    }
+  }
+}
+
+__device__ __noinline__ void inner_mixed_factor(const Args& a, Smem& sm, const float4* __restrict__ U, float4* __restrict__ w,
+                                   float2* __restrict__ x, float2* __restrict__ g, float2* __restrict__ d,
+                                   float2* __restrict__ q, char* dyn) {
+  const int W = a.W, nb = a.m.nb, c = threadIdx.x % W;
+  bc_solve<float>(a, sm, U, x, d, q, dyn);
+  for (int lev = 1; lev < a.bc_levels; ++lev) {
+    // e = U - S w into g; at the first refinement w = x1 is the FP32 vector x
+    if (lev == 1)
+      ff_residual(a, sm, U, x, g);
+    else
+      ff_residual(a, sm, U, w, g);
+    __syncthreads();  // every read of x / w for the residual is done
+    if (lev == 1) {
+      for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+        if (!sm.act[c]) continue;
+        const float2 xv = x[e];
+        w[e] = make_float4(xv.x, 0.f, xv.y, 0.f);
+      }
+      __syncthreads();
+    }
+    bc_solve<float>(a, sm, g, x, d, q, dyn);
+    for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+      if (!sm.act[c]) continue;
+      const float4 wv = w[e];
+      const float2 xv = x[e];
+      const gbff::ff re = gbff::ff_add(gbff::ff{wv.x, wv.y}, gbff::ff{xv.x, 0.f});
+      const gbff::ff im = gbff::ff_add(gbff::ff{wv.z, wv.w}, gbff::ff{xv.y, 0.f});
+      w[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+  }
+  if (a.bc_levels == 1) {
+    for (int e = threadIdx.x; e < 4 * nb * W; e += TPB) {
+      if (!sm.act[c]) continue;
+      const float2 xv = x[e];
+      w[e] = make_float4(xv.x, 0.f, xv.y, 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ inner solve, FP64
+// w = S^{-1} f: the exact factor solve where the factor exists, else CG.
+__device__ __noinline__ void inner64(const Args& a, Smem& sm, const double2* __restrict__ f, double2* __restrict__ x,
+                        double2* __restrict__ g, double2* __restrict__ d, double2* __restrict__ q, char* dyn) {
+  if (a.inner_bchol)
+    bc_solve<double>(a, sm, f, x, d, q, dyn);
+  else
+    cg64(a, sm, f, x, g, d, q);
 }
 
 }  // namespace gbk

@@ -143,18 +143,19 @@ def test_mixed_small(dev):
     check_outputs(out, ref, 1e-6)
 
 
-@pytest.mark.parametrize("flags", [0, 2, 4, 6])
+@pytest.mark.parametrize("flags", [0, 4, 6, 16, 18])
 def test_mixed_inner_method_and_placement(dev, flags):
-    # bit 2: CG instead of Chebyshev on the FP32 inner levels; bit 1: inner
-    # vectors in shared memory (they fit at this size).  Every combination
-    # must reach the oracle; the plan reports the placement.
+    # default: exact factor solves on the FP32 inner levels; bit 2: CG, bit 4:
+    # Chebyshev instead; bit 1: the iterations' vectors in shared memory (they
+    # fit at this size; the factor solve uses its own shared buffers).  Every
+    # combination must reach the oracle; the plan reports the placement.
     system = ppv_chain(4, seed=9)  # N = 152
     z = shift_grid(-10, 6, 40, 0.05)
     cols = np.arange(1, system.n, 9, dtype=np.int32)  # 17 columns: ragged last panel
     mat = gbg.Matrix(system)
     plan = gbg.solve_plan(mat, z, cols, prec="mixed", panel=4, flags=flags)
     mat.close()
-    assert plan["cg_smem"] == bool(flags & 2)
+    assert plan["cg_smem"] == bool(flags & 2 and flags & (4 | 16))
     out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=4, flags=flags)
     check_outputs(out, ref, 1e-6)
 
@@ -206,15 +207,17 @@ def test_indefinite_overlap_reported(dev):
 
 
 def test_correction_solve_fixes_stagnating_column(dev):
-    # Chain 331 of the uneven batch at eta 0.02 (N = 228, 115 shifts): the mixed
-    # path's residual for one column stagnates near a gap shift above tol 1e-6.
+    # Chain 331 of the uneven batch at eta 0.02 (N = 228, 115 shifts): with the
+    # iterative (Chebyshev, flags bit 4) inner solve the mixed path's residual
+    # for one column stagnates near a gap shift above tol 1e-6.
     # gb_correct_unconverged re-solves that column in FP64 with the stalled
     # shift as the seed; every pair must then meet tol and match the oracle.
     systems, problems = uneven_batch(eta=0.02)
     sysm, pr = systems[331], problems[331]
     assert sysm.n == 228 and len(pr["z"]) == 115
     mat = gbg.Matrix(sysm)
-    kw = dict(tol=1e-6, maxit=16000, prec="mixed", w_rho=pr["w_rho"], w_edm=pr["w_edm"], panel=2, want_g=True)
+    kw = dict(tol=1e-6, maxit=16000, prec="mixed", w_rho=pr["w_rho"], w_edm=pr["w_edm"], panel=2, want_g=True,
+              flags=16)
     first = gbg.shifted_solve(mat, pr["z"], pr["cols"], **kw)
     assert first["status"] == gbg._binding.GB_ENOCONV
     out = gbg.shifted_solve(mat, pr["z"], pr["cols"], correct=True, **kw)
@@ -227,18 +230,50 @@ def test_correction_solve_fixes_stagnating_column(dev):
     check_outputs(out, ref, 1e-6)
 
 
-@pytest.mark.parametrize("panel", [4, 8])
-def test_mixed_banded_cholesky_inner_solve(dev, panel):
-    # flags bit 3: the FP32 inner levels solve S x = r with the banded Cholesky
-    # factor (S's half-bandwidth is 53 here): one inner step per level, so the
-    # inner count is twice the outer count (plus the initial S^-1 b solve);
-    # outputs match the oracle.
-    system = ppv_chain(4, seed=9)  # N = 152
+@pytest.mark.parametrize("prec,panel,tol,per", [("mixed", 4, 1e-10, 4), ("mixed", 8, 1e-8, 3), ("mixed", 8, 1e-7, 2),
+                                                ("fp64", 4, 1e-12, 1), ("fp64", 32, 1e-12, 1)])
+def test_exact_factor_inner_solve(dev, prec, panel, tol, per):
+    # The default inner solve where S's half-bandwidth is <= 63 (53 here): the
+    # block-bidiagonal Cholesky factor, one solve per FP64 application; the
+    # mixed path refines FP32 solves around float-float residuals, two levels
+    # for tol >= 1e-7, three down to 1e-9 and four below.  The inner count is levels x (outer
+    # iterations + the initial S^-1 b); outputs match the oracle at each
+    # path's bound.  N = 152: three 64-row blocks, ragged last.
+    system = ppv_chain(4, seed=9)
     z = shift_grid(-10, 6, 40, 0.05)
     cols = np.arange(1, system.n, 9, dtype=np.int32)
-    out, ref = run_case(dev, system, z, cols, "mixed", 1e-10, 8000, panel=panel, flags=8)
-    check_outputs(out, ref, 1e-6)
+    bound = 1e-6 if prec == "mixed" else 1e-10
+    out, ref = run_case(dev, system, z, cols, prec, tol, 8000, panel=panel)
+    check_outputs(out, ref, bound)
     it = to_np(out["iters"])
     inner = to_np(out["inner_iters"])
     for p0 in range(0, len(cols), panel):
-        assert inner[p0] in (2 * it[p0 : p0 + panel].max(), 2 * (it[p0 : p0 + panel].max() + 1))
+        assert inner[p0] == per * (it[p0 : p0 + panel].max() + 1)
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("maker", [lambda: ppv_chain(7, seed=2), lambda: chain_4orb(41, seed=3)])
+def test_apply_sinv_exact(dev, maker, w):
+    # the factor solve alone: FP64 to rounding, one FP32 solve to ~4e-7
+    # (several 64-row blocks, ragged last block, every panel width)
+    system = maker()
+    mat = gbg.Matrix(system)
+    _, S = system.dense()
+    rng = np.random.default_rng(w)
+    x = rng.standard_normal((system.n, w)) + 1j * rng.standard_normal((system.n, w))
+    ref = np.linalg.solve(S, x)
+    xt = torch.from_numpy(x).to(dev)
+    y = to_np(mat.apply_sinv(xt, prec="fp64"))
+    assert rel(y, ref) < 1e-13
+    y32 = to_np(mat.apply_sinv(xt, prec="fp32"))
+    assert rel(y32, ref) < 2e-6
+    mat.close()
+
+
+def test_fp64_cg_inner_solve_still_matches(dev):
+    # flags bit 2 keeps the iterative inner CG (the path for wide-band S)
+    system = ppv_chain(3, seed=7)
+    z = shift_grid(-10, 6, 24, 0.05)
+    cols = np.arange(0, system.n, 11, dtype=np.int32)
+    out, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 5000, panel=4, flags=4)
+    check_outputs(out, ref, 1e-10)

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
     for name in names:
         assert hasattr(lib, name), name
     assert set(gbg.EXPORTED) <= set(names)
-    assert lib.gb_abi_version() == 1
+    assert lib.gb_abi_version() == 2
 
 
 def dense_from_blocks(b, n):
@@ -114,44 +114,65 @@ def test_gpu_entry_points_fail_loudly_without_a_device():
         gbg.Matrix(chain_4orb(4, seed=0))
 
 
-@pytest.mark.parametrize("maker", [lambda: chain_4orb(9, seed=1), lambda: ppv_chain(3, seed=4)])
-def test_band_cholesky_factor_reproduces_s(maker):
-    # the factor the flags-bit-3 inner solve uses: L L^T = S on the padded size
-    # (identity past n), band layout by columns (up) and rows (row) consistent
+def block_solve_host(f, rhs):
+    """Applies the factor the exact inner solve uses, in the order the kernel
+    does: t_i = Dinv_i r_i, y_i = t_i - E_i y_{i-1}; u_i = DinvT_i y_i,
+    x_i = u_i - F_i x_{i+1} (64-row blocks, k-major storage)."""
+    nblk = f["nblk"]
+    n64 = 64 * nblk
+    r = np.zeros((n64,) + rhs.shape[1:])
+    r[: rhs.shape[0]] = rhs
+    blk = lambda v, i: v[64 * i : 64 * i + 64]
+    # entry (r, k) of a block at [k, r]: the block's matrix is the transpose
+    y = np.zeros_like(r)
+    for i in range(nblk):
+        t = f["dinv"][i].T @ blk(r, i)
+        if i > 0:
+            t = t - f["e"][i].T @ blk(y, i - 1)
+        y[64 * i : 64 * i + 64] = t
+    x = np.zeros_like(r)
+    for i in reversed(range(nblk)):
+        u = f["dinvt"][i].T @ blk(y, i)
+        if i + 1 < nblk:
+            u = u - f["f"][i].T @ blk(x, i + 1)
+        x[64 * i : 64 * i + 64] = u
+    return x[: rhs.shape[0]]
+
+
+@pytest.mark.parametrize("maker", [lambda: chain_4orb(9, seed=1), lambda: ppv_chain(3, seed=4),
+                                   lambda: ppv_chain(7, seed=2), lambda: chain_4orb(41, seed=3)])
+def test_block_factor_solves_s_exactly(maker):
+    # The exact inner solve's factor: the block recurrences reproduce S^-1 r to
+    # FP64 rounding on the padded size (identity past n), the half-bandwidth
+    # is S's, the factor blocks have the triangular / band structure the
+    # kernel's loops rely on, and several 64-row blocks (ragged last block) occur.
     system = maker()
-    f = gbg.band_cholesky_to_host(system)
+    f = gbg.block_factor_to_host(system)
     _, S = system.dense()
     n = system.n
     n4 = 4 * ((n + 3) // 4)
     rows, cols = np.nonzero(np.tril(S))
-    assert f["bw"] == int((rows - cols).max())
-    bw = f["bw"]
-    L = np.zeros((n4, n4))
-    for i in range(n4):
-        L[i, i] = 1.0 / float(f["invd"][i])
-        for t in range(bw):
-            if i - 1 - t >= 0:
-                L[i, i - 1 - t] = f["row"][i, t]
-    for i in range(n4):
-        for t in range(bw):
-            if i + 1 + t < n4:
-                assert f["up"][i, t] == np.float32(L[i + 1 + t, i])
-    assert not f["up"][:, bw:].any() and not f["row"][:, bw:].any()
+    bw = int((rows - cols).max())
+    assert f["bw"] == bw and f["nblk"] == (n4 + 63) // 64
     Sp = np.eye(n4)
     Sp[:n, :n] = S
-    assert np.abs(L @ L.T - Sp).max() < 1e-5 * np.abs(Sp).max()
-    # solving with the FP32 factor is accurate to FP32 (the level's accuracy)
-    r = np.random.default_rng(0).standard_normal(n4)
-    x = np.linalg.solve(L.T, np.linalg.solve(L, r))
-    ref = np.linalg.solve(Sp, r)
-    assert np.abs(x - ref).max() < 1e-5 * np.abs(ref).max()
+    rhs = np.random.default_rng(0).standard_normal((n4, 3))
+    x = block_solve_host(f, rhs)
+    ref = np.linalg.solve(Sp, rhs)
+    assert np.abs(x - ref).max() < 1e-13 * np.abs(ref).max()
+    for i in range(f["nblk"]):
+        dinv = f["dinv"][i].T  # entry (r, k)
+        assert not np.triu(dinv, 1).any()  # lower triangular
+        assert np.array_equal(f["dinvt"][i], dinv)  # DinvT stored k-major is Dinv row-major
+        assert not f["e"][i][: 64 - bw].any()  # E only in the last bw columns (k >= 64 - bw)
+        assert not f["f"][i][bw:].any()  # F only in the first bw columns (k < bw)
+    assert not f["e"][0].any() and not f["f"][-1].any()
 
 
-def test_band_cholesky_reports_wide_band_unavailable():
+def test_block_factor_reports_wide_band_unavailable():
     bundle = ppv_bundle(n_side=2, n_mono=2, seed=1)
     _, S = bundle.dense()
     rows, cols = np.nonzero(np.tril(S))
     assert (rows - cols).max() > 63
-    f = gbg.band_cholesky_to_host(bundle)
-    assert f["bw"] == 0
-    assert not f["up"].any() and not f["row"].any() and not f["invd"].any()
+    f = gbg.block_factor_to_host(bundle)
+    assert f["bw"] == 0 and f["nblk"] == 0

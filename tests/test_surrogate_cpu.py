@@ -119,3 +119,45 @@ def test_descriptor_two_atom_hand_case():
     assert np.isclose(d[0, 56], 4 * 0.25)
     assert np.isclose(d[0, 59], 0.25 * sum(H[i, i] for i in others))
     assert np.isclose(d[0, 61], 0.05)
+
+
+def test_adam_second_step_by_hand():
+    # two steps, gradients 0.5 then -0.3 (lr 0.1, b1 0.9, b2 0.999, eps 1e-8),
+    # expanded by hand: m1 = 0.05, v1 = 2.5e-4; m2 = 0.9 * 0.05 - 0.1 * 0.3 =
+    # 0.015, v2 = 0.999 * 2.5e-4 + 0.001 * 0.09 = 3.3975e-4; bias corrections
+    # 1 - 0.9^2 = 0.19 and 1 - 0.999^2 = 0.001999
+    w1, m1, v1 = omlp.adam(np.array([1.0]), np.array([0.5]), np.zeros(1), np.zeros(1), 0.1, 0.9, 0.999, 1e-8, 1)
+    w2, m2, v2 = omlp.adam(w1, np.array([-0.3]), m1, v1, 0.1, 0.9, 0.999, 1e-8, 2)
+    assert np.isclose(m2[0], 0.015, rtol=1e-14) and np.isclose(v2[0], 3.3975e-4, rtol=1e-14)
+    step2 = 0.1 * (0.015 / 0.19) / (np.sqrt(3.3975e-4 / 0.001999) + 1e-8)
+    assert np.isclose(w2[0], w1[0] - step2, rtol=1e-14, atol=1e-16)
+    assert np.isclose(step2, 0.0191498, rtol=1e-5)  # hand value: 0.1 x 0.0789474 / 0.412262
+
+
+def test_descriptor_onsite_energy_bins_by_hand():
+    # three 1-orbital atoms far apart (> 0.5 nm: no radial features); row 0 has
+    # neighbours 1 and 2 with onsite energies placed on bin centres 3 and 6 of
+    # the eight onsite-energy bins (centres -3 + 6 t / 7, width 0.75):
+    # H_11 = -3/7, H_22 = 15/7.  Neighbour couplings H_01 = -0.5, H_02 = 0.2,
+    # S_01 = 0.1, S_02 = -0.05.  By hand, with (centre spacing 6/7) / 0.75 = 8/7:
+    #   f[48 + t] = 0.25 exp(-(8 (t - 3) / 7)^2) + 0.04 exp(-(8 (t - 6) / 7)^2)
+    #   f[57] = 0.1^2 + 0.05^2 = 0.0125      f[58] = -0.05 - 0.01 = -0.06
+    #   f[60] = 0.5 + 0.2 = 0.7             f[62] = 0.1 (-3/7) - 0.05 (15/7) = -0.15
+    #   f[56] = 0.29                        f[59] = 0.25 (-3/7) + 0.04 (15/7) = -0.15 / 7
+    n = 3
+    rp = np.array([0, 3, 6, 9], np.int64)
+    ci = np.tile(np.arange(3, dtype=np.int32), 3)
+    H = np.array([[0.7, -0.5, 0.2], [-0.5, -3.0 / 7.0, 0.3], [0.2, 0.3, 15.0 / 7.0]])
+    S = np.array([[1.0, 0.1, -0.05], [0.1, 1.0, 0.02], [-0.05, 0.02, 1.0]])
+    pos = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.0, 2.0, 0]])
+    system = TBSystem(n, rp, ci, H.ravel(), S.ravel(), np.arange(3, dtype=np.int32), positions=pos,
+                      atom_norb=np.ones(3, np.int32))
+    d = odesc.descriptors(system, np.ones(3, int))[0]
+    t = np.arange(8)
+    bins = 0.25 * np.exp(-((8 * (t - 3) / 7) ** 2)) + 0.04 * np.exp(-((8 * (t - 6) / 7) ** 2))
+    assert np.allclose(d[48:56], bins, rtol=1e-13, atol=0)
+    assert np.argmax(d[48:56]) == 3 and d[54] > 0.04 and d[54] < 0.0401
+    assert np.isclose(d[56], 0.29) and np.isclose(d[57], 0.0125) and np.isclose(d[58], -0.06)
+    assert np.isclose(d[59], -0.15 / 7) and np.isclose(d[60], 0.7) and np.isclose(d[62], -0.15)
+    assert np.isclose(d[46], 0.7) and np.isclose(d[47], 1.0) and np.isclose(d[61], 0.03)
+    assert not d[0:40].any()  # every neighbour atom is beyond the 0.5 nm cutoff
