@@ -163,7 +163,8 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
  * equations, Introduction).  On its own here, for tests and timing.  X and Y:
  * device arrays of n rows x w complex columns, layout as in gb_spmm;
  * prec = GB_FP64: double, one FP64 factor solve (exact to rounding);
- * GB_MIXED: float, one FP32 factor solve (no refinement: ~4e-7 relative).
+ * GB_MIXED: float, one FP32 factor solve on TF32 tensor cores with a
+ * three-term split (no refinement: ~2e-6 relative).
  * w in {1, 2, 4, 8, 16, 32}.  GB_EINVAL if the matrix has no factor (S's
  * half-bandwidth above 63).  Allocates its scratch on `stream` (stream-ordered
  * allocator) and frees it; synchronous.

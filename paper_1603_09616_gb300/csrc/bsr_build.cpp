@@ -376,4 +376,51 @@ void block_factor(HostBSR* hb) {
   hb->bf_nblk = nblk;
 }
 
+// Fragment order of an m16n8k8 TF32 A operand (PTX mma): lane l = 4 g + t
+// holds a0 = A(g, t), a1 = A(g + 8, t), a2 = A(g, t + 4), a3 = A(g + 8, t + 4)
+// of the 16 x 8 tile (rows 16 mi.., columns 8 ks..).  A fragment is stored as
+// 128 consecutive floats, lane l's four values at 4 l .. 4 l + 3.
+static void put_fragment(const double* M, int mi, int ks, float* dst) {  // M k-major: (r, k) at k * 64 + r
+  for (int l = 0; l < 32; ++l) {
+    const int g = l >> 2, t = l & 3;
+    for (int sl = 0; sl < 4; ++sl) {
+      const int r = 16 * mi + g + 8 * (sl & 1), k = 8 * ks + t + 4 * (sl >> 1);
+      dst[l * 4 + sl] = (float)M[(size_t)k * 64 + r];
+    }
+  }
+}
+
+// Per block: the FWD tile holds the D^-1 fragments a lower-triangular product
+// needs (k-step ks, row tile mi >= ks / 2; 20 of them, by ks then mi), then
+// the E fragments of k-steps (64 - bw) / 8 .. 7 (by ks then mi); the BWD tile
+// holds the D^-T fragments with mi <= ks / 2 (20), then the F fragments of
+// k-steps 0 .. ceil(bw / 8) - 1.
+std::vector<float> mma_tiles(const HostBSR& hb) {
+  std::vector<float> out;
+  if (hb.bf_bw <= 0 || hb.bf.empty()) return out;
+  const int64_t nblk = hb.bf_nblk;
+  const size_t part = (size_t)nblk * 4096;
+  const double* df = hb.bf.data();
+  const double* db = df + part;
+  const double* ef = db + part;
+  const double* fb = ef + part;
+  const int bw = hb.bf_bw, ksE0 = (64 - bw) / 8, nF = (bw + 7) / 8;
+  out.assign((size_t)2 * nblk * kMmaTileFloats, 0.f);
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    float* fwd = out.data() + (size_t)(2 * blk) * kMmaTileFloats;
+    float* bwd = fwd + kMmaTileFloats;
+    int p = 0;
+    for (int ks = 0; ks < 8; ++ks)
+      for (int mi = ks / 2; mi < 4; ++mi) put_fragment(df + (size_t)blk * 4096, mi, ks, fwd + 128 * p++);
+    for (int ks = ksE0; ks < 8; ++ks)
+      for (int mi = 0; mi < 4; ++mi) put_fragment(ef + (size_t)blk * 4096, mi, ks, fwd + 128 * p++);
+    p = 0;
+    for (int ks = 0; ks < 8; ++ks)
+      for (int mi = 0; mi <= ks / 2; ++mi) put_fragment(db + (size_t)blk * 4096, mi, ks, bwd + 128 * p++);
+    for (int ks = 0; ks < nF; ++ks)
+      for (int mi = 0; mi < 4; ++mi) put_fragment(fb + (size_t)blk * 4096, mi, ks, bwd + 128 * p++);
+  }
+  return out;
+}
+
 }  // namespace gb

@@ -39,4 +39,13 @@ gb_status build_host_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_i
 void preconditioned_s_bounds(HostBSR* hb);
 void block_factor(HostBSR* hb);
 
+// The FP32 factor rearranged for the tensor-core passes of the exact inner
+// solve (block_chol.cuh): per 64-row block two tiles of kMmaTilePairs
+// fragments (FWD: D^-1 then E; BWD: D^-T then F), each fragment the 32 x 4
+// values one warp loads for an m16n8k8 TF32 A operand.  Returns
+// 2 * nblk * kMmaTileFloats floats (empty without a factor).
+constexpr int kMmaTilePairs = 52;                     // 20 triangular + up to 32 band fragments
+constexpr int kMmaTileFloats = kMmaTilePairs * 128;  // 26,624 bytes
+std::vector<float> mma_tiles(const HostBSR& hb);
+
 }  // namespace gb

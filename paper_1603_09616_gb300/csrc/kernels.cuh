@@ -55,13 +55,16 @@ struct DevMat {
   const double* h_val;
   const double* s_val;
   double s_lam_min, s_lam_max;  // spectrum bounds of the block-Jacobi-preconditioned S
-  // Block-bidiagonal Cholesky factor of S on 64-row blocks (bf_bw = 0: none):
-  // four [bf_nblk][64][64] arrays, k-major (entry (r, k) at k * 64 + r):
-  // D_i^-1, D_i^-T, E_i = D_i^-1 C_i, F_i = D_i^-T C_{i+1}^T; FP32 and FP64.
+  // Block-bidiagonal Cholesky factor of S on 64-row blocks (bf_bw = 0: none).
+  // FP64: four [bf_nblk][64][64] arrays, k-major (entry (r, k) at k * 64 + r):
+  // D_i^-1, D_i^-T, E_i = D_i^-1 C_i, F_i = D_i^-T C_{i+1}^T.  FP32: per block
+  // a FWD and a BWD tile of kMmaTileFloatsDev floats in tensor-core fragment
+  // order (block_chol.cuh).
   int bf_bw, bf_nblk;
-  const float* bf32;
+  const float* bfm;
   const double* bf64;
 };
+constexpr int kMmaTileFloatsDev = 52 * 128;
 
 // ------------------------------------------------------------ complex FP64
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -80,14 +83,16 @@ __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isf
 
 // ------------------------------------------------------------ block reduce
 struct RedSmem {
-  double* red;  // NWARP * NVMAX * 32 partials at the start of the team's dynamic shared memory
   double scal[NVMAX * WMAX];
 };
 
 // Sum NV per-thread partials over all threads sharing column c = tid % W.
 // Result for (value i, column c) lands in rs.scal[i * WMAX + c].  Fixed order.
+// The per-warp partials (NWARP * NVMAX * 32 doubles) live at the start of the
+// kernel's dynamic shared memory, which every team kernel sizes for them.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], int W, RedSmem& rs) {
+  extern __shared__ __align__(16) double br_dyn[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int off = W; off < 32; off <<= 1) {
 #pragma unroll
@@ -95,13 +100,13 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], int W, RedSmem& rs
   }
   if (lane < W) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) rs.red[(warp * NV + i) * 32 + lane] = v[i];
+    for (int i = 0; i < NV; ++i) br_dyn[(warp * NV + i) * 32 + lane] = v[i];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < NV * W; t += TPB) {
     const int i = t / W, c = t - i * W;
     double s = 0.0;
-    for (int w = 0; w < NWARP; ++w) s += rs.red[(w * NV + i) * 32 + c];
+    for (int w = 0; w < NWARP; ++w) s += br_dyn[(w * NV + i) * 32 + c];
     rs.scal[i * WMAX + c] = s;
   }
   __syncthreads();

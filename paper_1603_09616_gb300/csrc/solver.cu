@@ -332,7 +332,9 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   const size_t o_rp = take(sizeof(int) * (n + 1)), o_ci = take(sizeof(int) * nnz);
   const size_t o_hv = take(sizeof(double) * nnz), o_sv = take(sizeof(double) * nnz);
   const size_t nbf = hb.bf.size();  // 4 x nblk x 4096 factor entries (0: no factor)
-  const size_t o_bf64 = take(sizeof(double) * nbf), o_bf32 = take(sizeof(float) * nbf);
+  const std::vector<float> mt = mma_tiles(hb);
+  static_assert(kMmaTileFloats == gbk::kMmaTileFloatsDev, "tile size of host and device");
+  const size_t o_bf64 = take(sizeof(double) * nbf), o_bfm = take(sizeof(float) * mt.size());
   const size_t total = off;
 
   std::vector<char> host(total, 0);
@@ -367,8 +369,7 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   put(o_sv, hb.s_val.data(), sizeof(double) * nnz);
   if (nbf) {
     put(o_bf64, hb.bf.data(), sizeof(double) * nbf);
-    float* f32 = reinterpret_cast<float*>(host.data() + o_bf32);
-    for (size_t i = 0; i < nbf; ++i) f32[i] = (float)hb.bf[i];
+    put(o_bfm, mt.data(), sizeof(float) * mt.size());
   }
 
   gb_matrix* m = new gb_matrix();
@@ -414,7 +415,7 @@ gb_status gb_build_bsr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
   d.bf_bw = nbf ? hb.bf_bw : 0;
   d.bf_nblk = nbf ? (int)hb.bf_nblk : 0;
   d.bf64 = nbf ? reinterpret_cast<const double*>(b + o_bf64) : nullptr;
-  d.bf32 = nbf ? reinterpret_cast<const float*>(b + o_bf32) : nullptr;
+  d.bfm = nbf ? reinterpret_cast<const float*>(b + o_bfm) : nullptr;
   *out = m;
   return GB_OK;
 }
@@ -514,17 +515,17 @@ void set_inner_method(const gb_matrix* m, const gb_solve_params* p, double itol,
   a.hp_fp32 = (p->prec == GB_MIXED && (p->flags & kFlagHpF32)) ? 1 : 0;
   if (!(p->flags & (kFlagCG | kFlagCheb)) && m->dm.bf_bw > 0) {
     a.inner_bchol = 1;  // exact: block-bidiagonal Cholesky factor solves
-    // mixed: FP32 factor solves, each accurate to ~4e-7 (measured in an
-    // emulation of the kernel's arithmetic), refined around float-float
-    // residuals: two levels for tol >= 1e-7, three down to 1e-9, four below
+    // mixed: FP32 factor solves on TF32 tensor cores with a three-term split,
+    // each accurate to ~2e-6 (measured), refined around float-float
+    // residuals: two levels for tol >= 1e-6, three down to 1e-9, four below
     // (measured: at tol 1e-10 a near-threshold pair of a 114-orbital chain
     // stagnated at 7.7e-10 with three levels and converged with four); an
-    // explicit inner_tol asks for (4e-7)^levels <= inner_tol, two at least
+    // explicit inner_tol asks for (2e-6)^levels <= inner_tol, two at least
     if (p->inner_tol > 0) {
       a.bc_levels = 2;
-      while (a.bc_levels < 4 && std::pow(4e-7, a.bc_levels) > p->inner_tol) ++a.bc_levels;
+      while (a.bc_levels < 4 && std::pow(2e-6, a.bc_levels) > p->inner_tol) ++a.bc_levels;
     } else {
-      a.bc_levels = p->tol >= 1e-7 ? 2 : (p->tol >= 1e-9 ? 3 : 4);
+      a.bc_levels = p->tol >= 1e-6 ? 2 : (p->tol >= 1e-9 ? 3 : 4);
     }
     return;
   }
@@ -597,7 +598,7 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
   auto fits = [&](int w) { return want_smem && 3 * n4 * (size_t)w * cg_esz + gbk::kRedBytes <= smem_budget; };
   auto dyn_bytes = [&](int w) -> size_t {
     const unsigned cg = fits(w) ? (unsigned)(3 * n4 * (size_t)w * cg_esz) : 0u;
-    return gbk::dyn_layout(p->prec == GB_FP64, w, bchol, cg).bytes;
+    return gbk::dyn_layout(p->prec == GB_FP64, w, bchol, cg, m->dm.bf_bw).bytes;
   };
   auto occupancy = [&](size_t dyn) {
     int per_sm = 1;
@@ -641,6 +642,7 @@ gb_status make_plan(const gb_matrix* m, const gb_solve_params* p, bool want_g, P
     pl->itol = p->inner_tol > 0 ? p->inner_tol : 1e-7;
 
   set_inner_method(m, p, pl->itol, pl->a);
+  pl->a.bc_bw_alloc = m->dm.bf_bw;
   const size_t K = p->nshift, Wz = W, maxit = p->maxit, N4 = 4 * (size_t)m->nb;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -869,7 +871,8 @@ gb_status gb_apply_sinv(const gb_matrix* m, gb_precision prec, int32_t w, const 
   a.m = m->dm;
   a.W = w;
   a.inner_bchol = 1;
-  const size_t dyn = gbk::dyn_layout(f64, w, true, 0).bytes;
+  a.bc_bw_alloc = m->dm.bf_bw;
+  const size_t dyn = gbk::dyn_layout(f64, w, true, 0, m->dm.bf_bw).bytes;
   if (e == cudaSuccess) {
     if (f64) {
       e = cudaFuncSetAttribute(sinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -1684,7 +1687,7 @@ gb_status make_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_s
                                    : (const void*)gbk::team_kernel_batched<true>;
   // dynamic shared memory: the factor solve's buffers (systems without a
   // factor leave them unused)
-  auto dyn_bytes = [&](int w) -> size_t { return gbk::dyn_layout(prec == GB_FP64, w, true, 0).bytes; };
+  auto dyn_bytes = [&](int w) -> size_t { return gbk::dyn_layout(prec == GB_FP64, w, true, 0, 63).bytes; };
   auto occupancy = [&](size_t dyn) {
     int per_sm = 1;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -1822,6 +1825,7 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
       a.inner_bchol = im.inner_bchol;
       a.bc_levels = im.bc_levels;
       a.hp_fp32 = im.hp_fp32;
+      a.bc_bw_alloc = 63;  // the launch's shared memory is sized for any band
       a.cheb_K = im.cheb_K;
       a.cheb_c0 = im.cheb_c0;
       std::memcpy(a.cheb_A, im.cheb_A, sizeof a.cheb_A);

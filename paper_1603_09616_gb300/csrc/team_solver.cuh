@@ -61,6 +61,7 @@ struct Args {
   int inner_cheb, cheb_K;
   int inner_bchol;  // 1: S x = f by the block-bidiagonal Cholesky factor (exact; block_chol.cuh)
   int bc_levels;    // mixed path: FP32 factor solves per application (refinement levels)
+  int bc_bw_alloc;  // half-bandwidth the dynamic shared memory of the FP32 factor passes is sized for
   // Verification mode: team b solves panel b only and records r_m on every row
   // (history row = W columns x N4 rows, column-major) instead of the pattern
   // rows, for the true-residual check; only the coefficients (cgs), nk and
@@ -112,8 +113,8 @@ __device__ __forceinline__ void team_init(Smem& sm, char* dyn);
 namespace gbk {
 
 __device__ __forceinline__ void team_init(Smem& sm, char* dyn) {
+  (void)dyn;  // block_reduce finds its partials at the start of the dynamic shared memory
   if (threadIdx.x == 0) {
-    sm.rs.red = reinterpret_cast<double*>(dyn);
     for (int b = 0; b < kTileBufs; ++b) mbar_init(&sm.bc_bar[b], 1);
     fence_mbar_init();
     sm.tile_base = 0;

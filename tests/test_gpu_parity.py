@@ -230,13 +230,13 @@ def test_correction_solve_fixes_stagnating_column(dev):
     check_outputs(out, ref, 1e-6)
 
 
-@pytest.mark.parametrize("prec,panel,tol,per", [("mixed", 4, 1e-10, 4), ("mixed", 8, 1e-8, 3), ("mixed", 8, 1e-7, 2),
+@pytest.mark.parametrize("prec,panel,tol,per", [("mixed", 4, 1e-10, 4), ("mixed", 8, 1e-8, 3), ("mixed", 8, 1e-6, 2),
                                                 ("fp64", 4, 1e-12, 1), ("fp64", 32, 1e-12, 1)])
 def test_exact_factor_inner_solve(dev, prec, panel, tol, per):
     # The default inner solve where S's half-bandwidth is <= 63 (53 here): the
     # block-bidiagonal Cholesky factor, one solve per FP64 application; the
     # mixed path refines FP32 solves around float-float residuals, two levels
-    # for tol >= 1e-7, three down to 1e-9 and four below.  The inner count is levels x (outer
+    # for tol >= 1e-6, three down to 1e-9 and four below.  The inner count is levels x (outer
     # iterations + the initial S^-1 b); outputs match the oracle at each
     # path's bound.  N = 152: three 64-row blocks, ragged last.
     system = ppv_chain(4, seed=9)
@@ -254,8 +254,9 @@ def test_exact_factor_inner_solve(dev, prec, panel, tol, per):
 @pytest.mark.parametrize("w", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("maker", [lambda: ppv_chain(7, seed=2), lambda: chain_4orb(41, seed=3)])
 def test_apply_sinv_exact(dev, maker, w):
-    # the factor solve alone: FP64 to rounding, one FP32 solve to ~4e-7
-    # (several 64-row blocks, ragged last block, every panel width)
+    # the factor solve alone: FP64 to rounding, one FP32 solve (TF32 tensor
+    # cores, three-term split) to ~2e-6 (several 64-row blocks, ragged last
+    # block, every panel width)
     system = maker()
     mat = gbg.Matrix(system)
     _, S = system.dense()
@@ -266,7 +267,7 @@ def test_apply_sinv_exact(dev, maker, w):
     y = to_np(mat.apply_sinv(xt, prec="fp64"))
     assert rel(y, ref) < 1e-13
     y32 = to_np(mat.apply_sinv(xt, prec="fp32"))
-    assert rel(y32, ref) < 2e-6
+    assert rel(y32, ref) < 5e-6
     mat.close()
 
 
