@@ -270,3 +270,68 @@ def test_sparse_oracle_matches_closed_form():
         for c, j in enumerate(cols):
             R = system.row_cols(int(j))
             assert np.allclose(sp_out[k, off[c] : off[c + 1]], G[R, j], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- chemical potential (oracle/fermi.py)
+def test_fermi_level_tends_to_the_eigenvalue_occupation():
+    # small eta, fine grid: the quadrature's mu tends to the mu that fills the
+    # generalized eigenvalues, sum_l 2 f((lambda_l - mu) / kT) = N_e, and
+    # rho to 2 sum_l f y_l y_l^T (the eigen-decomposition limit)
+    from oracle import fermi as of
+
+    system = chain_4orb(4, seed=12)  # N = 16
+    H, S, lam, Y = spectral(system)
+    kT, eta = 0.3, 4e-3
+    eps = np.arange(lam.min() - 3.0, lam.max() + 3.0, eta / 4)
+    z = eps + 1j * eta
+    n_e = float(system.n)  # one electron per orbital
+    # the eigenvalue occupation, by its own bisection on the spectrum
+    lo, hi = lam.min() - 10, lam.max() + 10
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if 2 * of.fermi((lam - mid) / kT).sum() < n_e:
+            lo = mid
+        else:
+            hi = mid
+    mu_eig = 0.5 * (lo + hi)
+    cols = np.arange(system.n)
+    X = oracle.green_columns(H, S, z, cols)
+    g = oracle.project_columns(system, X, cols)
+    zero = np.zeros(len(z), dtype=np.complex128)
+    ldos = oracle.reduce_outputs(system, g, cols, zero, zero)["ldos"]
+    mu = of.fermi_level(z.real, ldos, n_e, kT)
+    assert abs(mu - mu_eig) < 2e-2, (mu, mu_eig)
+    c, ce = of.weights(z.real, mu, kT)
+    out = oracle.reduce_outputs(system, g, cols, c, ce)
+    assert abs(out["q"].sum() - n_e) < 1e-9 * n_e  # Tr[rho S] = N_e exactly at the found mu
+    P = 2 * (Y * of.fermi((lam - mu_eig) / kT)) @ Y.T
+    err = max(np.abs(out["rho"][out["off"][c_] : out["off"][c_ + 1]] - P[system.row_cols(j), j]).max()
+              for c_, j in enumerate(cols))
+    assert err < 3e-2, err
+
+
+def test_fermi_level_two_site_half_filled_level_and_planted_spin():
+    # 2-site case, S = I: levels e - |t| and e + |t|.  One electron (spin 2)
+    # half-fills the lower level, so mu sits on it (f is antisymmetric about
+    # the level and its Lorentzian is symmetric in a window centred on it; the
+    # upper level's tail moves mu by ~1e-4 here)
+    from oracle import fermi as of
+    from synth import TBSystem
+
+    e, t = 0.4, -1.5
+    lower = e - abs(t)
+    rp = np.array([0, 2, 4], np.int64)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    sysm = TBSystem(2, rp, ci, np.array([e, t, t, e]), np.array([1.0, 0.0, 0.0, 1.0]), np.array([0, 1], np.int32))
+    eps = np.linspace(lower - 4.0, lower + 4.0, 3201)
+    z = eps + 1j * 0.01
+    H, S = sysm.dense()
+    X = oracle.green_columns(H, S, z, np.arange(2))
+    g = oracle.project_columns(sysm, X, np.arange(2))
+    zero = np.zeros(len(z), dtype=np.complex128)
+    ldos = oracle.reduce_outputs(sysm, g, np.arange(2), zero, zero)["ldos"]
+    mu = of.fermi_level(z.real, ldos, 1.0, kT=0.05)
+    assert abs(mu - lower) < 2e-3, mu
+    # a dropped spin factor would need the whole lower level: mu leaves it
+    mu1 = of.fermi_level(z.real, ldos, 1.0, kT=0.05, spin=1.0)
+    assert mu1 > lower + 0.2, mu1
