@@ -322,6 +322,38 @@ gb_status gb_true_residual(const gb_matrix* m, const gb_solve_params* p, int32_t
 size_t gb_true_residual_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t nver);
 
 /*
+ * gb_fermi_density — chemical potential from the electron count, and the
+ * Fermi-weighted density and energy-density matrices of a finished solve.
+ *
+ * The molecular dynamics of the paper needs the density matrix of the
+ * occupied states at every step (Quantum molecular dynamics simulation); the
+ * occupation needs the chemical potential mu, fixed by the electron count.
+ * From a solve of EVERY orbital (p->nrhs = n, each orbital once) that kept
+ * G_ij(z_k) (out.g_proj of gb_shifted_solve) and the local DOS, on an evenly
+ * spaced real-axis grid z_k = eps_k + i eta (spacing d), with
+ * f(x) = 1 / (1 + e^x) and spin degeneracy `spin`:
+ *   c_k = -(spin / pi) f((eps_k - mu) / kT) d,   c^E_k = eps_k c_k,
+ *   N(mu) = sum_j q_j = -pi sum_k c_k sum_j ldos[k][j]   (increasing in mu),
+ * mu solves N(mu) = n_electrons (bisection to FP64 resolution), and
+ *   rho_ij = sum_k c_k Im G_ij(z_k),  edm_ij = sum_k c^E_k Im G_ij(z_k),
+ *   q_j = sum_i rho_ij S_ij,  e_loc_j = sum_i rho_ij H_ij,
+ * all from the same solve (no second solve).
+ *   g_proj, ldos  device outputs of that solve ([K][P][2], [K][nrhs])
+ *   mu            host: the chemical potential
+ *   out           its rho, edm, q, e_loc (device, caller-owned, any may be NULL
+ *                 except that q / e_loc need rho) are overwritten
+ *   workspace     gb_fermi_workspace_size(m, p) bytes, 256-byte aligned
+ * GB_EINVAL if the shifts are not evenly spaced, or the electron count lies
+ * outside what the grid holds.  Synchronous.
+ */
+gb_status gb_fermi_density(const gb_matrix* m, const gb_solve_params* p, const double* g_proj, const double* ldos,
+                           double n_electrons, double kT, double spin, double* mu, const gb_outputs* out,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of workspace gb_fermi_density needs (0: invalid arguments). */
+size_t gb_fermi_workspace_size(const gb_matrix* m, const gb_solve_params* p);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
  * The shifted equations of the Introduction for many independent structures

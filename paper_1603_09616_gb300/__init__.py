@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     GBError,
     Matrix,
     block_factor_to_host,
+    fermi_density,
     bsr_to_host,
     load,
     pattern_offsets,

@@ -38,6 +38,8 @@ EXPORTED = (
     "gb_static_scratch_bytes",
     "gb_shifted_solve_batched",
     "gb_true_residual",
+    "gb_fermi_density",
+    "gb_fermi_workspace_size",
     "gb_true_residual_workspace_size",
     "gb_correct_unconverged",
     "gb_correct_workspace_size",
@@ -131,6 +133,12 @@ def load() -> C.CDLL:
                                      C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32)]
     lib.gb_true_residual_workspace_size.restype = C.c_size_t
     lib.gb_true_residual_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
+    lib.gb_fermi_density.restype = C.c_int
+    lib.gb_fermi_density.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_double,
+                                     C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(Outputs), C.c_void_p,
+                                     C.c_size_t, C.c_void_p]
+    lib.gb_fermi_workspace_size.restype = C.c_size_t
+    lib.gb_fermi_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
     lib.gb_shifted_solve_static.restype = C.c_int
     lib.gb_shifted_solve_static.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.POINTER(Outputs), C.c_void_p]
     lib.gb_static_scratch_bytes.restype = C.c_size_t
@@ -413,6 +421,42 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
         res["status"] = st
         res["message"] = lib.gb_last_error().decode()
         res["corrected"] = int(fixed.value)
+    return res
+
+
+def fermi_density(mat: Matrix, z, cols, solved: dict, n_electrons: float, kT: float, spin: float = 2.0,
+                  stream=None) -> dict:
+    """Chemical potential and Fermi-weighted rho / edm / q / e_loc from a
+    finished solve of every orbital (``solved`` = the result of
+    :func:`shifted_solve` with ``want_g=True``): gb_fermi_density."""
+    import torch
+
+    if solved.get("g_proj") is None:
+        raise ValueError("the solve must keep g_proj (want_g=True)")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    p = _params(z, cols, 1e-10, 1, "fp64", None, None, 0.0, 0, -1, keep)
+    lib = load()
+    need = lib.gb_fermi_workspace_size(mat.handle, C.byref(p))
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    P = int(solved["off"][-1])
+    nrhs = p.nrhs
+    f64 = dict(dtype=torch.float64, device=dev)
+    res = dict(rho=torch.empty(P, **f64), edm=torch.empty(P, **f64), q=torch.empty(nrhs, **f64),
+               e_loc=torch.empty(nrhs, **f64))
+    o = Outputs()
+    for f, _ in Outputs._fields_:
+        t = res.get(f)
+        setattr(o, f, C.c_void_p(t.data_ptr()) if t is not None else None)
+    mu = C.c_double(0.0)
+    _check(lib.gb_fermi_density(mat.handle, C.byref(p), C.c_void_p(solved["g_proj"].data_ptr()),
+                                C.c_void_p(solved["ldos"].data_ptr()), float(n_electrons), float(kT), float(spin),
+                                C.byref(mu), C.byref(o), C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()),
+                                _stream_handle(stream)))
+    res["mu"] = float(mu.value)
+    res["off"] = solved["off"]
     return res
 
 

@@ -1188,6 +1188,168 @@ gb_status gb_true_residual(const gb_matrix* m, const gb_solve_params* p, int32_t
 
 }  // extern "C"
 
+// ------------------------------------------------------------ chemical potential
+// mu from the electron count and the Fermi-weighted rho / P^E of a finished
+// solve of every orbital (Quantum molecular dynamics simulation: the density
+// matrix of each MD step).  Real-axis rule on an evenly spaced shift grid
+// z_k = eps_k + i eta, spacing d: c_k = -(s / pi) f((eps_k - mu) / kT) d,
+// c^E_k = eps_k c_k, and N(mu) = sum_j q_j = -pi sum_k c_k D_k with the total
+// DOS D_k = sum_j ldos[k][j], increasing in mu: bisection on the host over the
+// K values D_k, then the reductions of rho / P^E / q / E on the device from
+// the kept G_ij(z_k).
+namespace {
+
+__global__ void __launch_bounds__(256) dos_sum_kernel(const double* __restrict__ ldos, int K, int nrhs,
+                                                      double* __restrict__ dos) {
+  __shared__ double part[256];
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nrhs; j += 256) acc += ldos[(size_t)k * nrhs + j];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {  // fixed-order tree
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dos[k] = part[0];
+}
+
+// rho_e = sum_k c_k Im G_e(z_k), edm_e = sum_k eps_k c_k Im G_e(z_k) for every
+// kept pattern entry e (the weights are real).
+__global__ void __launch_bounds__(256) fermi_density_kernel(const double2* __restrict__ g, long long P, int K,
+                                                            const double* __restrict__ c,
+                                                            const double* __restrict__ eps,
+                                                            double* __restrict__ rho, double* __restrict__ edm) {
+  const long long e = blockIdx.x * 256LL + threadIdx.x;
+  if (e >= P) return;
+  double r = 0.0, en = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double im = g[(size_t)k * P + e].y;
+    r = fma(c[k], im, r);
+    en = fma(eps[k] * c[k], im, en);
+  }
+  if (rho) rho[e] = r;
+  if (edm) edm[e] = en;
+}
+
+__global__ void __launch_bounds__(256) local_sums_kernel(const gbk::DevMat m, const int* __restrict__ cols,
+                                                         const long long* __restrict__ off, int nrhs,
+                                                         const double* __restrict__ rho, double* __restrict__ q,
+                                                         double* __restrict__ el) {
+  const int c = blockIdx.x * 256 + threadIdx.x;
+  if (c >= nrhs) return;
+  const int j = cols[c], base = m.row_ptr[j], mc = m.row_ptr[j + 1] - base;
+  double qs = 0.0, es = 0.0;
+  for (int t = 0; t < mc; ++t) {
+    const double r = rho[off[c] + t];
+    qs = fma(r, m.s_val[base + t], qs);
+    es = fma(r, m.h_val[base + t], es);
+  }
+  if (q) q[c] = qs;
+  if (el) el[c] = es;
+}
+
+double fermi_f(double x) { return x >= 0 ? std::exp(-x) / (1.0 + std::exp(-x)) : 1.0 / (1.0 + std::exp(x)); }
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_fermi_workspace_size(const gb_matrix* m, const gb_solve_params* p) {
+  clear_error();
+  if (!m || !p || p->nshift < 1 || p->nrhs < 1) {
+    fail(GB_EINVAL, "NULL argument or empty problem");
+    return 0;
+  }
+  return align256(8 * (size_t)p->nshift) * 3 + align256(4 * (size_t)p->nrhs) + align256(8 * ((size_t)p->nrhs + 1)) +
+         256;
+}
+
+gb_status gb_fermi_density(const gb_matrix* m, const gb_solve_params* p, const double* g_proj, const double* ldos,
+                           double n_electrons, double kT, double spin, double* mu, const gb_outputs* out,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!m || !p || !g_proj || !ldos || !mu || !out) return fail(GB_EINVAL, "NULL argument");
+  const int K = p->nshift, nrhs = p->nrhs;
+  if (K < 2 || !p->z_re || !p->z_im) return fail(GB_EINVAL, "need at least two shifts");
+  if (nrhs != m->n || !p->rhs_cols) return fail(GB_EINVAL, "the electron count needs every orbital solved (nrhs = n)");
+  {
+    std::vector<char> seen(m->n, 0);
+    for (int c = 0; c < nrhs; ++c) {
+      const int j = p->rhs_cols[c];
+      if (j < 0 || j >= m->n || seen[j]) return fail(GB_EINVAL, "rhs_cols must hold every orbital once");
+      seen[j] = 1;
+    }
+  }
+  const double d = (p->z_re[K - 1] - p->z_re[0]) / (K - 1);
+  if (!(d > 0.0)) return fail(GB_EINVAL, "shift real parts must increase");
+  for (int k = 0; k < K; ++k)
+    if (!std::isfinite(p->z_re[k]) || std::fabs(p->z_re[k] - (p->z_re[0] + k * d)) > 1e-9 * std::fabs(d) * K ||
+        !(p->z_im[k] > 0.0))
+      return fail(GB_EINVAL, "the shifts must be evenly spaced in Re z with Im z > 0");
+  if (!(kT > 0.0) || !(spin > 0.0) || !(n_electrons > 0.0) || !(n_electrons < spin * m->n))
+    return fail(GB_EINVAL, "need kT > 0, spin > 0 and 0 < n_electrons < spin * n");
+  const size_t need = gb_fermi_workspace_size(m, p);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < need) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  double* d_dos = reinterpret_cast<double*>(w);
+  double* d_c = reinterpret_cast<double*>(w + align256(8 * (size_t)K));
+  double* d_eps = reinterpret_cast<double*>(w + 2 * align256(8 * (size_t)K));
+  int* d_cols = reinterpret_cast<int*>(w + 3 * align256(8 * (size_t)K));
+  long long* d_off = reinterpret_cast<long long*>(w + 3 * align256(8 * (size_t)K) + align256(4 * (size_t)nrhs));
+  dos_sum_kernel<<<K, 256, 0, s>>>(ldos, K, nrhs, d_dos);
+  GB_CUDA(cudaGetLastError());
+  std::vector<double> dos(K);
+  GB_CUDA(cudaMemcpyAsync(dos.data(), d_dos, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  auto count = [&](double x) {
+    double n = 0.0;
+    for (int k = 0; k < K; ++k) n += spin * fermi_f((p->z_re[k] - x) / kT) * d * dos[k];  // -pi c_k D_k
+    return n;
+  };
+  double lo = p->z_re[0] - 40.0 * kT, hi = p->z_re[K - 1] + 40.0 * kT;
+  if (!(count(lo) <= n_electrons && n_electrons <= count(hi)))
+    return fail(GB_EINVAL, "the electron count is outside what the shift grid can hold (%g..%g)", count(lo), count(hi));
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count(mid) < n_electrons)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *mu = 0.5 * (lo + hi);
+  std::vector<double> c(K), eps(K);
+  for (int k = 0; k < K; ++k) {
+    eps[k] = p->z_re[k];
+    c[k] = -(spin / 3.141592653589793238462643383279502884) * fermi_f((eps[k] - *mu) / kT) * d;
+  }
+  std::vector<long long> off(nrhs + 1, 0);
+  for (int i = 0; i < nrhs; ++i) {
+    const int j = p->rhs_cols[i];
+    off[i + 1] = off[i] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+  }
+  const long long P = off[nrhs];
+  GB_CUDA(cudaMemcpyAsync(d_c, c.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_eps, eps.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_cols, p->rhs_cols, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nrhs + 1), cudaMemcpyHostToDevice, s));
+  fermi_density_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(g_proj), P, K,
+                                                                   d_c, d_eps, out->rho, out->edm);
+  GB_CUDA(cudaGetLastError());
+  if (out->rho && (out->q || out->e_loc)) {
+    local_sums_kernel<<<(unsigned)((nrhs + 255) / 256), 256, 0, s>>>(m->dm, d_cols, d_off, nrhs, out->rho, out->q,
+                                                                     out->e_loc);
+    GB_CUDA(cudaGetLastError());
+  }
+  GB_CUDA(cudaStreamSynchronize(s));  // the host vectors above are this call's locals
+  return GB_OK;
+}
+
+}  // extern "C"
+
 // ------------------------------------------------------------ correction solve
 // Shifted COCG with one seed can stagnate for a shift whose shifted residual
 // loses attainable accuracy (observed near the gap of some PPV-like chains at
