@@ -266,9 +266,9 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
  * breakdown or an indefinite S are left alone).  The paper's equation is the
  * same (Introduction); the correction is this library's answer to shifted
  * COCG's limited attainable accuracy: each such column is solved again alone,
- * in plain FP64 (exact factor inner solve where available), with its worst
- * unconverged shift (largest resid) as the seed.  While shifts still miss
- * tol, the worst remaining one seeds the next solve (six seeds at most), and
+ * in plain FP64 (exact factor inner solve where available), first with the
+ * first solve's seed.  While shifts still miss tol, the worst remaining one
+ * that has not been a seed yet seeds the next solve (six seeds at most), and
  * every shift keeps the result of the seed that served it best (its G_ij(z_k)
  * on the pattern row; rho, edm, q and e_loc are formed from those).  The
  * column's ldos, rho, edm, q, e_loc, iters and inner_iters (summed over the

@@ -197,6 +197,196 @@ __global__ void __launch_bounds__(256, WC == 4 ? 6 : 8)
   }
 }
 
+// FP64 narrow panels (W = 1, 2), same quad layout as the FP32 kernel above:
+// lane l accumulates row l mod 4 of the blocks b0 + floor(l / 4) + 8k, so a
+// warp step reads 8 whole consecutive blocks (1 KB of values) and the 4 lanes
+// of a block share its x gather.  The product is bound by the FP64 FMA pipe
+// (GB300 runs FP64 at 1/64 of its FP32 rate), so the layout's job is to keep
+// enough loads in flight that the pipe never waits: two 8-block steps per lane.
+template <int WC>
+__global__ void __launch_bounds__(256, 4)
+    spmm_quad_d_kernel(const gbk::DevMat m, const double* __restrict__ A, const double2* __restrict__ x,
+                       double2* __restrict__ y) {
+  const long long I = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (I >= m.nb) return;  // uniform per warp
+  const int lane = threadIdx.x & 31, r = lane & 3, s = lane >> 2;
+  constexpr int U = 2;
+  constexpr int NX = 4 * WC;  // double2 per gathered 4 x WC complex x block
+  double2 acc[WC];
+#pragma unroll
+  for (int c = 0; c < WC; ++c) acc[c] = make_double2(0.0, 0.0);
+  const int b1 = m.blk_ptr[I + 1];
+  const double2* __restrict__ A2 = reinterpret_cast<const double2*>(A);
+  auto step = [&](const double2 (&a)[2], const double2 (&xv)[NX]) {
+    const double ar[4] = {a[0].x, a[0].y, a[1].x, a[1].y};
+#pragma unroll
+    for (int c = 0; c < WC; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[c].x = fma(ar[t], xv[t * WC + c].x, acc[c].x);
+        acc[c].y = fma(ar[t], xv[t * WC + c].y, acc[c].y);
+      }
+  };
+  int b = m.blk_ptr[I] + s;
+  for (; b + 8 * (U - 1) < b1; b += 8 * U) {
+    int J[U];
+    double2 a[U][2], xv[U][NX];
+#pragma unroll
+    for (int u = 0; u < U; ++u) J[u] = __ldcs(m.blk_col + b + 8 * u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      a[u][0] = __ldcs(A2 + (size_t)(b + 8 * u) * 8 + 2 * r);
+      a[u][1] = __ldcs(A2 + (size_t)(b + 8 * u) * 8 + 2 * r + 1);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < NX; ++q) xv[u][q] = __ldg(x + (size_t)J[u] * NX + q);
+#pragma unroll
+    for (int u = 0; u < U; ++u) step(a[u], xv[u]);
+  }
+  for (; b < b1; b += 8) {
+    const int J = __ldcs(m.blk_col + b);
+    const double2 a[2] = {__ldcs(A2 + (size_t)b * 8 + 2 * r), __ldcs(A2 + (size_t)b * 8 + 2 * r + 1)};
+    double2 xv[NX];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) xv[q] = __ldg(x + (size_t)J * NX + q);
+    step(a, xv);
+  }
+#pragma unroll
+  for (int off = 4; off < 32; off <<= 1)
+#pragma unroll
+    for (int c = 0; c < WC; ++c) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
+    }
+  if (s == 0 && 4 * I + r < m.n) {
+#pragma unroll
+    for (int c = 0; c < WC; ++c) y[(size_t)(4 * I + r) * WC + c] = acc[c];
+  }
+}
+
+// Wide panels (FP32: W = 4..64 in powers of two; FP64: W = 4..32): one warp
+// per block row, split into G = 32 / CL groups of CL lanes; group g takes the
+// blocks b0 + g + G k, and lane c of a group owns columns [c * PC, (c+1) * PC)
+// of the panel (PC = 2 complex columns per lane in FP32, read and written as
+// one float4; 1 in FP64).  A block's values are read by every lane of its
+// group at one address (a broadcast), its x rows by the group as contiguous
+// runs, and each value feeds PC complex columns from registers.  The groups
+// then add up through xor shuffles.  Requires x and y 16-byte aligned.
+template <int CL>
+__global__ void __launch_bounds__(256, 2)
+    spmm_wide_kernel(const gbk::DevMat m, const float* __restrict__ A, const float4* __restrict__ x,
+                     float4* __restrict__ y) {
+  constexpr int G = 32 / CL;
+  const long long I = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (I >= m.nb) return;
+  const int lane = threadIdx.x & 31, g = lane / CL, c = lane - g * CL;
+  float4 acc[4];  // row r: (re, im) of columns 2c and 2c + 1
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4* __restrict__ A4 = reinterpret_cast<const float4*>(A);
+  auto step = [&](const float4 (&a)[4], const float4 (&xv)[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float ar[4] = {a[r].x, a[r].y, a[r].z, a[r].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[r].x = fmaf(ar[t], xv[t].x, acc[r].x);
+        acc[r].y = fmaf(ar[t], xv[t].y, acc[r].y);
+        acc[r].z = fmaf(ar[t], xv[t].z, acc[r].z);
+        acc[r].w = fmaf(ar[t], xv[t].w, acc[r].w);
+      }
+    }
+  };
+  const int b1 = m.blk_ptr[I + 1];
+  int b = m.blk_ptr[I] + g;
+  constexpr int U = 2;
+  for (; b + G * (U - 1) < b1; b += G * U) {
+    int J[U];
+    float4 a[U][4], xv[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) J[u] = __ldcs(m.blk_col + b + G * u);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[u][r] = __ldcs(A4 + (size_t)(b + G * u) * 4 + r);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) xv[u][t] = __ldg(x + (size_t)(4 * J[u] + t) * CL + c);
+#pragma unroll
+    for (int u = 0; u < U; ++u) step(a[u], xv[u]);
+  }
+  for (; b < b1; b += G) {
+    const int J = __ldcs(m.blk_col + b);
+    float4 a[4], xv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = __ldcs(A4 + (size_t)b * 4 + r);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = __ldg(x + (size_t)(4 * J + t) * CL + c);
+    step(a, xv);
+  }
+#pragma unroll
+  for (int off = CL; off < 32; off <<= 1)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+      acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+      acc[r].z += __shfl_xor_sync(0xffffffffu, acc[r].z, off);
+      acc[r].w += __shfl_xor_sync(0xffffffffu, acc[r].w, off);
+    }
+  if (g == 0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (4 * I + r < m.n) y[(size_t)(4 * I + r) * CL + c] = acc[r];
+  }
+}
+
+template <int CL>
+__global__ void __launch_bounds__(256, 3)
+    spmm_wide_d_kernel(const gbk::DevMat m, const double* __restrict__ A, const double2* __restrict__ x,
+                       double2* __restrict__ y) {
+  constexpr int G = 32 / CL;
+  const long long I = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (I >= m.nb) return;
+  const int lane = threadIdx.x & 31, g = lane / CL, c = lane - g * CL;
+  double2 acc[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_double2(0.0, 0.0);
+  const double2* __restrict__ A2 = reinterpret_cast<const double2*>(A);
+  const int b1 = m.blk_ptr[I + 1];
+  for (int b = m.blk_ptr[I] + g; b < b1; b += G) {
+    const int J = __ldcs(m.blk_col + b);
+    double2 a[8], xv[4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = __ldcs(A2 + (size_t)b * 8 + q);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xv[t] = __ldg(x + (size_t)(4 * J + t) * CL + c);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const double ar[4] = {a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[r].x = fma(ar[t], xv[t].x, acc[r].x);
+        acc[r].y = fma(ar[t], xv[t].y, acc[r].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = CL; off < 32; off <<= 1)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+      acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+    }
+  if (g == 0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (4 * I + r < m.n) y[(size_t)(4 * I + r) * CL + c] = acc[r];
+  }
+}
+
 template <bool F64>
 __global__ void spmm_kernel(const gbk::DevMat m, int which, int W, const void* __restrict__ xv,
                             void* __restrict__ yv) {
@@ -473,19 +663,40 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
   const long long work = w <= 8 ? (long long)m->nb * 32 : (long long)m->nb * w;  // threads of work
   const int blocks = (int)std::min<long long>((work + threads - 1) / threads, (long long)nsm * 8);
-  const bool quad = prec != GB_FP64 && (w == 1 || w == 2 || w == 4) &&
-                    (reinterpret_cast<uintptr_t>(xin) % 16) == 0;
-  if (quad) {
+  const bool aligned = (reinterpret_cast<uintptr_t>(xin) % 16) == 0 && (reinterpret_cast<uintptr_t>(y) % 16) == 0;
+  const bool pow2 = (w & (w - 1)) == 0;
+  const unsigned wblocks = (unsigned)((m->nb + 7) / 8);  // 8 warps = 8 block rows per CTA
+  if (aligned && prec != GB_FP64 && w <= 2) {
     const float* A = which ? m->dm.sb_hi : m->dm.hb_hi;
     const auto* xq = static_cast<const float2*>(xin);
     auto* yq = static_cast<float2*>(y);
-    const unsigned qblocks = (unsigned)((m->nb + 7) / 8);  // 8 warps = 8 block rows per CTA
     if (w == 1)
-      spmm_quad_kernel<1><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
-    else if (w == 2)
-      spmm_quad_kernel<2><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+      spmm_quad_kernel<1><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq);
     else
-      spmm_quad_kernel<4><<<qblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+      spmm_quad_kernel<2><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq);
+  } else if (aligned && prec != GB_FP64 && pow2) {  // w = 4 .. 64
+    const float* A = which ? m->dm.sb_hi : m->dm.hb_hi;
+    const auto* xq = static_cast<const float4*>(xin);
+    auto* yq = static_cast<float4*>(y);
+    switch (w) {
+      case 4: spmm_wide_kernel<2><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 8: spmm_wide_kernel<4><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 16: spmm_wide_kernel<8><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 32: spmm_wide_kernel<16><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      default: spmm_wide_kernel<32><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+    }
+  } else if (aligned && prec == GB_FP64 && pow2 && w <= 32) {
+    const double* A = which ? m->dm.sb : m->dm.hb;
+    const auto* xq = static_cast<const double2*>(xin);
+    auto* yq = static_cast<double2*>(y);
+    switch (w) {
+      case 1: spmm_quad_d_kernel<1><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 2: spmm_quad_d_kernel<2><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 4: spmm_wide_d_kernel<4><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 8: spmm_wide_d_kernel<8><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      case 16: spmm_wide_d_kernel<16><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+      default: spmm_wide_d_kernel<32><<<wblocks, threads, 0, s>>>(m->dm, A, xq, yq); break;
+    }
   } else if (prec == GB_FP64) {
     spmm_kernel<true><<<blocks, threads, 0, s>>>(m->dm, which, w, xin, y);
   } else {
@@ -1476,15 +1687,26 @@ gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, c
     }
     int it_sum = 0, in_sum = 0, rounds = 0;
     bool done = false;
+    std::vector<char> tried(K, 0);
     for (int round = 0; round < kMaxSeeds && !done; ++round) {
-      int kw = -1;  // the worst shift still missing tol becomes the seed
-      double rw = -1.0;
-      for (int k = 0; k < K; ++k)
-        if (cur[k] > p->tol && cur[k] > rw) {
-          rw = cur[k];
-          kw = k;
-        }
-      if (kw < 0) kw = K / 2;
+      // First the first solve's own seed, now in FP64 with the exact inner
+      // solve (this alone converges most stalled columns); then the worst
+      // shift still missing tol that has not been a seed yet.  (A shift that
+      // stalls as a non-seed shift can stall as the seed too, so the worst
+      // shift is not the first choice.)
+      int kw = -1;
+      if (round == 0) {
+        kw = p->seed_shift >= 0 ? p->seed_shift : K / 2;
+      } else {
+        double rw = -1.0;
+        for (int k = 0; k < K; ++k)
+          if (!tried[k] && cur[k] > p->tol && cur[k] > rw) {
+            rw = cur[k];
+            kw = k;
+          }
+        if (kw < 0) break;  // every failing shift has been a seed
+      }
+      tried[kw] = 1;
       gb_solve_params q = *p;
       q.nrhs = 1;
       q.rhs_cols = &col;

@@ -34,7 +34,7 @@ def dev():
 
 # ------------------------------------------------------------------ SpMM
 @pytest.mark.parametrize("system_fn", [lambda: chain_4orb(37, seed=2), lambda: ppv_chain(5, seed=4)])
-@pytest.mark.parametrize("w", [1, 2, 3, 4, 16, 64])
+@pytest.mark.parametrize("w", [1, 2, 3, 4, 8, 16, 32, 64])
 def test_spmm_fp64_and_fp32(dev, system_fn, w):
     system = system_fn()
     mat = gbg.Matrix(system)
@@ -50,10 +50,10 @@ def test_spmm_fp64_and_fp32(dev, system_fn, w):
     mat.close()
 
 
-@pytest.mark.parametrize("w", [1, 2, 4])
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16])
 def test_spmm_fp32_unaligned_x_matches_aligned(dev, w):
     # x starting 8 bytes past a 16-byte boundary cannot take the float4-gather
-    # kernel of the narrow FP32 panels; both kernels must give the product
+    # kernels of the FP32 panels; both kernels must give the product
     # (n % 4 == 0 here, so x is read in place, not through a padded copy)
     system = chain_4orb(37, seed=2)
     assert system.n % 4 == 0
