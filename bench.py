@@ -433,7 +433,7 @@ def run_chain800(gbg, torch):
 
 
 # ---------------------------------------------------------------- SpMM bandwidth
-def measure_spmm(gbg, torch, widths=(1, 2, 4, 8, 16), reps=10):
+def measure_spmm(gbg, torch, widths=(1, 2, 4, 8, 16, 32, 64), reps=10):
     """gb_spmm (Y = H X) on the condensed-bundle Hamiltonian (N = 321,100).
 
     Algorithmic bytes per launch: v*nnz (values) + 4*nnzb (block columns)
@@ -443,9 +443,9 @@ def measure_spmm(gbg, torch, widths=(1, 2, 4, 8, 16), reps=10):
     only together with the matrix (>= 300 MB per launch), so every launch
     streams from HBM.
     """
-    from synth import ppv_bundle
+    from synth import workload
 
-    system = ppv_bundle(seed=3)
+    system = workload("bundle169")["system"]
     mat = gbg.Matrix(system)
     info = mat.info
     n, nnz, nnzb, nb = info["n"], info["nnz"], info["nnzb"], info["nb"]
@@ -456,8 +456,8 @@ def measure_spmm(gbg, torch, widths=(1, 2, 4, 8, 16), reps=10):
     rows = []
     for prec, v in (("fp32", 4), ("fp64", 8)):
         for w in widths:
-            if prec == "fp64" and w > 2:
-                continue  # FP64 is ALU-bound on GB300 beyond the smallest panels
+            if prec == "fp64" and w > 8:
+                continue  # FP64 is FMA-bound at every width; wider panels only scale the time
             dt = torch.complex64 if prec == "fp32" else torch.complex128
             x = torch.randn(n, w, dtype=dt, device="cuda")
             y = torch.empty_like(x)

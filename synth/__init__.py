@@ -13,6 +13,7 @@ geometry here is a synthetic planar 14-atom phenylene-vinylene unit.
 """
 from .tb import (  # noqa: F401
     TBSystem,
+    align_blocks,
     chain_4orb,
     ppv_chain,
     ppv_bundle,

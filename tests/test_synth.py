@@ -71,3 +71,23 @@ def test_uneven_batch_is_deterministic():
         assert np.allclose(p["z"].imag, 0.02)
     again, _ = uneven_batch(eta=0.02)
     assert np.array_equal(again[331].h_val, systems[331].h_val)
+
+
+def test_align_blocks_is_a_permutation_that_aligns_every_carbon():
+    from synth import align_blocks
+
+    p = ppv_chain(7, seed=3)
+    a = align_blocks(p)
+    perm = a.meta["orbital_perm"]
+    assert np.array_equal(np.sort(perm), np.arange(p.n))
+    H, S = p.dense()
+    H2, S2 = a.dense()
+    assert np.array_equal(H[np.ix_(perm, perm)], H2)
+    assert np.array_equal(S[np.ix_(perm, perm)], S2)
+    # every 4-orbital atom occupies one whole aligned block
+    starts = np.concatenate([[0], np.cumsum(a.atom_norb)[:-1]])
+    assert np.all(starts[a.atom_norb == 4] % 4 == 0)
+    assert np.array_equal(np.bincount(a.orb_atom), a.atom_norb)
+    # the band of S stays within the 63 of the block factor
+    Sc = a.s_csr().tocoo()
+    assert np.abs(Sc.row - Sc.col).max() <= 63
