@@ -67,3 +67,45 @@ def test_fermi_rejects_partial_columns_and_uneven_grid():
     with pytest.raises(gbg.GBError, match="EINVAL"):
         gbg.fermi_density(mat, zu, cols, solved, 8.0, 0.1)
     mat.close()
+
+
+def test_fermi_density_tends_to_the_eigen_decomposition_limit():
+    # Small eta on a fine grid (256 shifts, spacing 1.5 eta) over a compressed
+    # spectrum (H scaled by 0.1, span 2.7 eV): the device's mu and rho approach
+    # the sharp-level values mu_eig (sum_l 2 f((lambda_l - mu) / kT) = N_e) and
+    # 2 sum_l f y_l y_l^T, and equal the oracle on the same rule to FP64 rounding.
+    import dataclasses
+
+    import scipy.linalg as sla
+
+    torch.cuda.set_device(0)
+    base = chain_4orb(4, seed=12)  # N = 16
+    system = dataclasses.replace(base, h_val=base.h_val * 0.1)
+    H, S = system.dense()
+    lam, Y = sla.eigh(H, S)
+    eta, kT = 0.01, 0.1
+    z = np.linspace(lam.min() - 0.6, lam.max() + 0.6, 256) + 1j * eta
+    n_e = float(system.n)
+    lo, hi = lam.min() - 10, lam.max() + 10
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if 2 * ofermi.fermi((lam - mid) / kT).sum() < n_e:
+            lo = mid
+        else:
+            hi = mid
+    mu_eig = 0.5 * (lo + hi)
+    cols = np.arange(system.n, dtype=np.int32)
+    mat = gbg.Matrix(system)
+    solved = gbg.shifted_solve(mat, z, cols, tol=1e-12, maxit=4000, prec="fp64", want_g=True)
+    assert solved["status"] == 0, solved["message"]
+    fd = gbg.fermi_density(mat, z, cols, solved, n_e, kT)
+    ref = ofermi.fermi_outputs(system, z, n_e, kT)
+    assert abs(fd["mu"] - ref["mu"]) < 1e-9
+    assert rel(fd["rho"].cpu().numpy(), ref["rho"]) < 1e-10
+    assert abs(fd["mu"] - mu_eig) < 5e-3, (fd["mu"], mu_eig)
+    P = 2 * (Y * ofermi.fermi((lam - mu_eig) / kT)) @ Y.T
+    rho = fd["rho"].cpu().numpy()
+    off = fd["off"]
+    err = max(np.abs(rho[off[c] : off[c + 1]] - P[system.row_cols(int(j)), j]).max() for c, j in enumerate(cols))
+    assert err < 5e-2, err
+    mat.close()
