@@ -663,7 +663,8 @@ def run_batched(args):
     gb_shifted_solve_batched launch whose panel width the library's autotuner
     picks from {8, 16, 32} (probe runs of 40 iterations, outside the timed
     region), followed by the FP64 correction solve of any column that misses
-    tol.  Timed: the launch plus the correction (CUDA events).  Then the same
+    tol.  Timed: the launch plus the correction (CUDA events; the correction's
+    share is reported as correct_ms).  Chains numbered by align_blocks.  Then the same
     batch in plain FP64 for the ratio.  Solves/s = sum over chains of shifts x
     right-hand sides / time."""
     import torch
@@ -672,7 +673,7 @@ def run_batched(args):
     from synth import uneven_batch
 
     torch.cuda.set_device(0)
-    systems, problems = uneven_batch(eta=0.02, cols_per_chain=8)
+    systems, problems = uneven_batch(eta=0.02, cols_per_chain=8, align=True)
     mats = [gbg.Matrix(s) for s in systems]
     stream = torch.cuda.current_stream()
     _, tinfo = gbg.shifted_solve_batched(mats, problems, prec="mixed", tune_probe_maxit=40)
@@ -698,6 +699,7 @@ def run_batched(args):
         ms = sum(times) / len(times)
         iters = np.concatenate([r["iters"].cpu().numpy() for r in res])
         out[prec] = {"value": pairs / (ms / 1e3), "ms": ms, "corrected_columns": info.get("corrected", 0),
+                     "correct_ms": info.get("correct_ms", 0.0),
                      "krylov_iters_per_s": float(iters.sum()) / (ms / 1e3),
                      "outer_iters": {"min": int(iters.min()), "median": int(np.median(iters)),
                                      "max": int(iters.max())}}

@@ -376,6 +376,30 @@ size_t gb_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, con
                                  int32_t panel, int32_t want_g);
 
 /*
+ * gb_correct_batched — the correction solve of a finished gb_shifted_solve_batched
+ * (same systems, params and outputs).  Every column, of every system, whose
+ * shifts missed tol (col_status bit 4, no breakdown, S definite) is solved again
+ * in ONE batched launch: plain FP64, exact factor inner solve where available,
+ * the first solve's seed, one column per panel.  The columns that then meet tol
+ * replace their entries in `outs` (ldos, rho, edm, q, e_loc, iters,
+ * inner_iters, converged, resid, g_proj, col_status).  Columns that still miss
+ * tol go through gb_correct_unconverged (seed switching), system by system.
+ *
+ * `workspace`: gb_correct_batched_workspace_size(...) bytes for the same
+ * arguments, 256-byte aligned.  Both calls read every system's col_status from
+ * the device (they wait on `stream`).  `ncorrected` (host, may be NULL): columns
+ * that now meet tol.  Returns GB_OK when every column meets tol, GB_ENOCONV if
+ * some still miss it.  Synchronous.
+ */
+gb_status gb_correct_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                             const gb_outputs* outs, void* workspace, size_t workspace_bytes, void* stream,
+                             int32_t* ncorrected);
+
+/* Bytes of workspace gb_correct_batched needs now (256 if no column failed; 0: invalid arguments). */
+size_t gb_correct_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                         const gb_outputs* outs, void* stream);
+
+/*
  * gb_tune_panel_batched — autotuner for the batched panel width: runs the
  * batch with every maxit capped at probe_maxit for panel widths {8, 16, 32},
  * times each launch on `stream`, and returns the fastest in *best_panel

@@ -39,6 +39,8 @@ EXPORTED = (
     "gb_shifted_solve_batched",
     "gb_true_residual",
     "gb_fermi_density",
+    "gb_correct_batched",
+    "gb_correct_batched_workspace_size",
     "gb_fermi_workspace_size",
     "gb_true_residual_workspace_size",
     "gb_correct_unconverged",
@@ -133,6 +135,11 @@ def load() -> C.CDLL:
                                      C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int32)]
     lib.gb_true_residual_workspace_size.restype = C.c_size_t
     lib.gb_true_residual_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
+    lib.gb_correct_batched.restype = C.c_int
+    lib.gb_correct_batched.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                       C.c_void_p, C.POINTER(C.c_int32)]
+    lib.gb_correct_batched_workspace_size.restype = C.c_size_t
+    lib.gb_correct_batched_workspace_size.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.gb_fermi_density.restype = C.c_int
     lib.gb_fermi_density.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_double,
                                      C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(Outputs), C.c_void_p,
@@ -343,9 +350,9 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
     residual is checked after the solve (gb_true_residual); ``resid_true``
     [K, len(verify)] then holds it, and columns that miss tol become
     unconverged in the outputs.  With ``correct=True`` a GB_ENOCONV result
-    (from the solve or the check) is passed to gb_correct_unconverged (FP64
-    re-solve of the failing columns with a switched seed); ``corrected`` then
-    holds the number of columns it fixed.
+    (from the solve or the check) is passed to gb_correct_batched (one FP64
+    re-solve of all failing columns, then seed switching for the rest);
+    ``corrected`` then holds the number of columns it fixed.
     """
     import torch
 
@@ -409,13 +416,17 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
             res["status"] = st
             res["message"] = f"{nflag.value} checked column(s) miss tol by their true residual"
     if correct and st == GB_ENOCONV:
-        cneed = lib.gb_correct_workspace_size(mat.handle, C.byref(p), int(want_g))
+        h1 = (C.c_void_p * 1)(mat.handle.value)
+        p1 = (SolveParams * 1)(p)
+        o1 = (Outputs * 1)(o)
+        sh = _stream_handle(stream)
+        cneed = lib.gb_correct_batched_workspace_size(1, h1, p1, o1, sh)
         if cneed == 0:
             raise GBError(GB_EINVAL, lib.gb_last_error().decode())
         cws = workspace if workspace.numel() >= cneed else torch.empty(int(cneed), dtype=torch.uint8, device=dev)
         fixed = C.c_int32(0)
-        st = lib.gb_correct_unconverged(mat.handle, C.byref(p), C.byref(o), C.c_void_p(cws.data_ptr()),
-                                        C.c_size_t(cws.numel()), _stream_handle(stream), C.byref(fixed))
+        st = lib.gb_correct_batched(1, h1, p1, o1, C.c_void_p(cws.data_ptr()), C.c_size_t(cws.numel()), sh,
+                                    C.byref(fixed))
         if st in raise_on:
             _check(st)
         res["status"] = st
@@ -558,8 +569,8 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
     w_rho, w_edm (one per matrix in ``mats``).  With ``tune_probe_maxit > 0``
     the panel width is first picked by the library's autotuner
     (gb_tune_panel_batched) on probe runs of that many iterations.  With
-    ``correct=True`` a GB_ENOCONV batch is passed system by system to
-    gb_correct_unconverged.  Returns a list of per-system result dicts plus the
+    ``correct=True`` a GB_ENOCONV batch goes to gb_correct_batched (one FP64
+    launch over every failing column, then seed switching where needed).  Returns a list of per-system result dicts plus the
     batch status/message/panel (and ``corrected`` columns).
     """
     import torch
@@ -606,25 +617,23 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
         _check(st)
     msg = lib.gb_last_error().decode()
     if correct and st == GB_ENOCONV:
-        fixed_total, left = 0, 0
-        for s_, mat in enumerate(mats):
-            cneed = lib.gb_correct_workspace_size(mat.handle, C.byref(params[s_]), int(want_g))
-            if cneed == 0:
-                raise GBError(GB_EINVAL, lib.gb_last_error().decode())
-            if workspace.numel() < cneed:
-                workspace = torch.empty(int(cneed), dtype=torch.uint8, device=dev)
-            fixed = C.c_int32(0)
-            r = lib.gb_correct_unconverged(mat.handle, C.byref(params[s_]), C.byref(outs[s_]),
-                                           C.c_void_p(workspace.data_ptr()), C.c_size_t(workspace.numel()),
-                                           _stream_handle(stream), C.byref(fixed))
-            if r in (GB_EINVAL, GB_ENOMEM, GB_ECUDA):
-                _check(r)
-            fixed_total += int(fixed.value)
-            if r != GB_OK:
-                left += 1
-                msg = f"system {s_}: " + lib.gb_last_error().decode()
-        st = GB_OK if left == 0 else GB_ENOCONV
-        msg = "" if left == 0 else msg
-        info["corrected"] = fixed_total
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sh = _stream_handle(stream)
+        cneed = lib.gb_correct_batched_workspace_size(nsys, handles, params, outs, sh)
+        if cneed == 0:
+            raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+        if workspace.numel() < cneed:
+            workspace = torch.empty(int(cneed), dtype=torch.uint8, device=dev)
+        fixed = C.c_int32(0)
+        st = lib.gb_correct_batched(nsys, handles, params, outs, C.c_void_p(workspace.data_ptr()),
+                                    C.c_size_t(workspace.numel()), sh, C.byref(fixed))
+        if st not in (GB_OK, GB_ENOCONV):
+            _check(st)
+        e1.record()
+        torch.cuda.synchronize()
+        msg = "" if st == GB_OK else lib.gb_last_error().decode()
+        info["corrected"] = int(fixed.value)
+        info["correct_ms"] = e0.elapsed_time(e1)
     info.update(status=st, message=msg, panel=panel, workspace=workspace)
     return results, info

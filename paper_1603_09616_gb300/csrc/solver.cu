@@ -141,18 +141,17 @@ __device__ __forceinline__ void quad_fma(const float4& a, const float4 (&xv)[2 *
   }
 }
 
-// Measured on the bundle Hamiltonian (N = 321,100): the kernel is bound by
-// loads in flight, so W = 1, 2 run two 8-block steps per lane at 32 registers
-// (64 warps per SM); W = 4 runs one step at 40 registers (48 warps), since at
-// 32 its spills cost more than the extra warps gain.
+// The kernel is bound by loads in flight: the block columns are fetched a
+// step ahead, W = 1 keeps two 8-block steps in flight per lane and W = 2 one,
+// at 40 registers (48 warps per SM) without spills.
 template <int WC>
-__global__ void __launch_bounds__(256, WC == 4 ? 6 : 8)
+__global__ void __launch_bounds__(256, 6)
     spmm_quad_kernel(const gbk::DevMat m, const float* __restrict__ A, const float2* __restrict__ x,
                      float2* __restrict__ y) {
   const long long I = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (I >= m.nb) return;  // uniform per warp
   const int lane = threadIdx.x & 31, r = lane & 3, s = lane >> 2;
-  constexpr int U = WC == 4 ? 1 : 2;  // steps of 8 blocks in flight per lane
+  constexpr int U = WC == 1 ? 2 : 1;  // steps of 8 blocks in flight per lane
   constexpr int NQ = 2 * WC;  // float4 per gathered 4 x WC complex x block
   float2 acc[WC];
 #pragma unroll
@@ -161,11 +160,20 @@ __global__ void __launch_bounds__(256, WC == 4 ? 6 : 8)
   const float4* __restrict__ A4 = reinterpret_cast<const float4*>(A);
   const float4* __restrict__ X4 = reinterpret_cast<const float4*>(x);
   int b = m.blk_ptr[I] + s;
+  // block columns one step ahead: the x gathers of a step then wait for one
+  // memory round trip, not two (column index, then x)
+  int Jn[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) Jn[u] = b + 8 * u < b1 ? __ldcs(m.blk_col + b + 8 * u) : 0;
   for (; b + 8 * (U - 1) < b1; b += 8 * U) {
     int J[U];
     float4 a[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) J[u] = __ldcs(m.blk_col + b + 8 * u);
+    for (int u = 0; u < U; ++u) {
+      J[u] = Jn[u];
+      const int bn = b + 8 * U + 8 * u;
+      Jn[u] = bn < b1 ? __ldcs(m.blk_col + bn) : 0;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) a[u] = __ldcs(A4 + (size_t)(b + 8 * u) * 4 + r);
     float4 xv[U][NQ];
@@ -177,8 +185,10 @@ __global__ void __launch_bounds__(256, WC == 4 ? 6 : 8)
     for (int u = 0; u < U; ++u) quad_fma<WC>(a[u], xv[u], acc);
   }
   for (; b < b1; b += 8) {
-    const int J = __ldcs(m.blk_col + b);
+    const int J = Jn[0];  // the loop above leaves the next step's columns in Jn
     const float4 a = __ldcs(A4 + (size_t)b * 4 + r);
+#pragma unroll
+    for (int u = 0; u + 1 < U; ++u) Jn[u] = Jn[u + 1];
     float4 xv[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) xv[q] = __ldg(X4 + (size_t)J * NQ + q);
@@ -302,11 +312,18 @@ __global__ void __launch_bounds__(256, 2)
   const int b1 = m.blk_ptr[I + 1];
   int b = m.blk_ptr[I] + g;
   constexpr int U = 2;
+  int Jn[U];  // block columns one step ahead (one round trip per step)
+#pragma unroll
+  for (int u = 0; u < U; ++u) Jn[u] = b + G * u < b1 ? __ldcs(m.blk_col + b + G * u) : 0;
   for (; b + G * (U - 1) < b1; b += G * U) {
     int J[U];
     float4 a[U][4], xv[U][4];
 #pragma unroll
-    for (int u = 0; u < U; ++u) J[u] = __ldcs(m.blk_col + b + G * u);
+    for (int u = 0; u < U; ++u) {
+      J[u] = Jn[u];
+      const int bn = b + G * U + G * u;
+      Jn[u] = bn < b1 ? __ldcs(m.blk_col + bn) : 0;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -319,7 +336,9 @@ __global__ void __launch_bounds__(256, 2)
     for (int u = 0; u < U; ++u) step(a[u], xv[u]);
   }
   for (; b < b1; b += G) {
-    const int J = __ldcs(m.blk_col + b);
+    const int J = Jn[0];
+#pragma unroll
+    for (int u = 0; u + 1 < U; ++u) Jn[u] = Jn[u + 1];
     float4 a[4], xv[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) a[r] = __ldcs(A4 + (size_t)b * 4 + r);
@@ -2328,6 +2347,236 @@ gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, cons
   cudaEventDestroy(e1);
   clear_error();
   if (*best_panel == 0) return fail(GB_ENOMEM, "no candidate panel width fits the workspace");
+  return GB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched correction
+// The correction of a finished batched launch: every column that missed tol,
+// of every system, is solved again in one batched FP64 launch (exact inner
+// solve, the first solve's seed, one column per panel), and the columns that
+// now meet tol are copied into the batch's outputs.  Columns that still miss
+// tol then go through gb_correct_unconverged (seed switching), system by
+// system.  The layout of the temporaries depends on which columns failed, so
+// the plan reads every system's col_status first.
+namespace {
+
+struct CorrBatch {
+  std::vector<int> sys;                      // sub-system -> system
+  std::vector<std::vector<int32_t>> cols;    // failing orbital columns per sub-system
+  std::vector<std::vector<int>> cidx;        // their positions in the system's column list
+  std::vector<std::vector<long long>> soff;  // packed pattern offsets of the sub-system
+  std::vector<gb_solve_params> q;
+  std::vector<gb_outputs> t;                 // temporaries, as offsets from the workspace base
+  size_t tmp_bytes = 0, batch_bytes = 0, single_bytes = 0, total = 0;
+};
+
+gb_status corr_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                          const gb_outputs* outs, cudaStream_t s, CorrBatch* cb) {
+  if (nsys < 1 || !mats || !params || !outs) return fail(GB_EINVAL, "NULL argument or empty batch");
+  for (int i = 0; i < nsys; ++i) {
+    const gb_solve_params* p = &params[i];
+    if (!mats[i] || !outs[i].col_status || !outs[i].resid || !p->rhs_cols || p->nrhs < 1)
+      return fail(GB_EINVAL, "system %d: matrix, col_status, resid and rhs_cols are required", i);
+    std::vector<int32_t> st(p->nrhs);
+    GB_CUDA(cudaMemcpyAsync(st.data(), outs[i].col_status, sizeof(int32_t) * p->nrhs, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> fc;
+    std::vector<int> ci;
+    for (int c = 0; c < p->nrhs; ++c)
+      if ((st[c] & gbk::kStNoConv) && !(st[c] & (gbk::kStBreakdown | gbk::kStNotSPD))) {
+        fc.push_back(p->rhs_cols[c]);
+        ci.push_back(c);
+      }
+    if (fc.empty()) continue;
+    cb->sys.push_back(i);
+    cb->cols.push_back(std::move(fc));
+    cb->cidx.push_back(std::move(ci));
+  }
+  const int nsub = (int)cb->sys.size();
+  size_t off = 0;
+  cb->q.resize(nsub);
+  cb->t.assign(nsub, gb_outputs{});
+  cb->soff.resize(nsub);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return reinterpret_cast<void*>(o + 256);  // +256: a null offset stays distinguishable
+  };
+  for (int u = 0; u < nsub; ++u) {
+    const int i = cb->sys[u];
+    const gb_matrix* m = mats[i];
+    const gb_outputs& o = outs[i];
+    gb_solve_params q = params[i];
+    q.nrhs = (int32_t)cb->cols[u].size();
+    q.rhs_cols = cb->cols[u].data();
+    q.prec = GB_FP64;
+    q.panel = 1;
+    q.flags = 0;
+    q.inner_tol = 0.0;
+    cb->q[u] = q;
+    const size_t K = q.nshift, n = q.nrhs;
+    std::vector<long long>& so = cb->soff[u];
+    so.assign(n + 1, 0);
+    for (size_t c = 0; c < n; ++c) {
+      const int j = cb->cols[u][c];
+      so[c + 1] = so[c] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+    }
+    const size_t P = so[n];
+    gb_outputs& t = cb->t[u];
+    if (o.ldos) t.ldos = static_cast<double*>(take(8 * K * n));
+    if (o.rho) t.rho = static_cast<double*>(take(8 * P));
+    if (o.edm) t.edm = static_cast<double*>(take(8 * P));
+    if (o.q) t.q = static_cast<double*>(take(8 * n));
+    if (o.e_loc) t.e_loc = static_cast<double*>(take(8 * n));
+    t.iters = static_cast<int32_t*>(take(4 * n));
+    t.inner_iters = static_cast<int32_t*>(take(4 * n));
+    t.col_status = static_cast<int32_t*>(take(4 * n));
+    if (o.converged) t.converged = static_cast<uint8_t*>(take(K * n));
+    t.resid = static_cast<double*>(take(8 * K * n));
+    if (o.g_proj) t.g_proj = static_cast<double*>(take(16 * K * P));
+  }
+  cb->tmp_bytes = align256(off + 256);
+  bool want_g = false;
+  for (int u = 0; u < nsub; ++u) want_g |= outs[cb->sys[u]].g_proj != nullptr;
+  if (nsub > 0) {
+    std::vector<const gb_matrix*> sm(nsub);
+    for (int u = 0; u < nsub; ++u) sm[u] = mats[cb->sys[u]];
+    cb->batch_bytes = gb_batched_workspace_size(nsub, sm.data(), cb->q.data(), 1, want_g ? 1 : 0);
+    if (cb->batch_bytes == 0) return GB_EINVAL;  // error text set by the size call
+    for (int u = 0; u < nsub; ++u) {
+      const int i = cb->sys[u];
+      const size_t b = gb_correct_workspace_size(mats[i], &params[i], outs[i].g_proj != nullptr);
+      if (b == 0) return GB_EINVAL;
+      cb->single_bytes = std::max(cb->single_bytes, b);
+    }
+  }
+  cb->total = std::max(cb->tmp_bytes + cb->batch_bytes, cb->single_bytes);
+  return GB_OK;
+}
+
+template <typename T>
+T* at(void* base, T* rel) {
+  return rel ? reinterpret_cast<T*>(static_cast<char*>(base) + (reinterpret_cast<uintptr_t>(rel) - 256)) : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_correct_batched_workspace_size(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                                         const gb_outputs* outs, void* stream) {
+  clear_error();
+  CorrBatch cb;
+  if (corr_batch_plan(nsys, mats, params, outs, static_cast<cudaStream_t>(stream), &cb) != GB_OK) return 0;
+  return std::max<size_t>(cb.total, 256);
+}
+
+gb_status gb_correct_batched(int32_t nsys, const gb_matrix* const* mats, const gb_solve_params* params,
+                             const gb_outputs* outs, void* workspace, size_t workspace_bytes, void* stream,
+                             int32_t* ncorrected) {
+  clear_error();
+  if (ncorrected) *ncorrected = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CorrBatch cb;
+  gb_status st = corr_batch_plan(nsys, mats, params, outs, s, &cb);
+  if (st != GB_OK) return st;
+  const int nsub = (int)cb.sys.size();
+  if (nsub == 0) return GB_OK;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < cb.total) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, cb.total);
+  char* base = static_cast<char*>(workspace);
+  std::vector<gb_outputs> tv(nsub);
+  std::vector<const gb_matrix*> sm(nsub);
+  for (int u = 0; u < nsub; ++u) {
+    const gb_outputs& r = cb.t[u];
+    gb_outputs& t = tv[u];
+    t.ldos = at(base, r.ldos);
+    t.rho = at(base, r.rho);
+    t.edm = at(base, r.edm);
+    t.q = at(base, r.q);
+    t.e_loc = at(base, r.e_loc);
+    t.iters = at(base, r.iters);
+    t.inner_iters = at(base, r.inner_iters);
+    t.col_status = at(base, r.col_status);
+    t.converged = at(base, r.converged);
+    t.resid = at(base, r.resid);
+    t.g_proj = at(base, r.g_proj);
+    sm[u] = mats[cb.sys[u]];
+  }
+  st = gb_shifted_solve_batched(nsub, sm.data(), cb.q.data(), tv.data(), 1, base + cb.tmp_bytes, cb.batch_bytes,
+                                stream);
+  if (st != GB_OK && st != GB_ENOCONV) return st;
+  int fixed = 0;
+  std::vector<int> left;
+  for (int u = 0; u < nsub; ++u) {
+    const int i = cb.sys[u];
+    const gb_solve_params* p = &params[i];
+    const gb_outputs& o = outs[i];
+    const gb_outputs& t = tv[u];
+    const int n = cb.q[u].nrhs, K = p->nshift, nrhs = p->nrhs;
+    std::vector<int32_t> tst(n);
+    GB_CUDA(cudaMemcpyAsync(tst.data(), t.col_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    // packed offsets of the system's own column list
+    std::vector<long long> ooff(nrhs + 1, 0);
+    for (int c = 0; c < nrhs; ++c) {
+      const int j = p->rhs_cols[c];
+      ooff[c + 1] = ooff[c] + (mats[i]->h_row_ptr[j + 1] - mats[i]->h_row_ptr[j]);
+    }
+    const long long Po = ooff[nrhs], Pt = cb.soff[u][n];
+    bool rest = false;
+    for (int a = 0; a < n; ++a) {
+      if (tst[a] & (gbk::kStNoConv | gbk::kStBreakdown | gbk::kStNotSPD)) {
+        rest = true;
+        continue;
+      }
+      const int c = cb.cidx[u][a];
+      const long long mc = ooff[c + 1] - ooff[c];
+      auto col2d = [&](void* dst, const void* src, size_t esz) {  // [K][nrhs] column c <- [K][n] column a
+        return cudaMemcpy2DAsync(static_cast<char*>(dst) + esz * c, esz * nrhs,
+                                 static_cast<const char*>(src) + esz * a, esz * n, esz, K, cudaMemcpyDeviceToDevice, s);
+      };
+      auto one = [&](void* dst, const void* src, size_t esz) {
+        return cudaMemcpyAsync(static_cast<char*>(dst) + esz * c, static_cast<const char*>(src) + esz * a, esz,
+                               cudaMemcpyDeviceToDevice, s);
+      };
+      if (o.ldos) GB_CUDA(col2d(o.ldos, t.ldos, 8));
+      if (o.converged) GB_CUDA(col2d(o.converged, t.converged, 1));
+      GB_CUDA(col2d(o.resid, t.resid, 8));
+      if (o.rho)
+        GB_CUDA(cudaMemcpyAsync(o.rho + ooff[c], t.rho + cb.soff[u][a], 8 * mc, cudaMemcpyDeviceToDevice, s));
+      if (o.edm)
+        GB_CUDA(cudaMemcpyAsync(o.edm + ooff[c], t.edm + cb.soff[u][a], 8 * mc, cudaMemcpyDeviceToDevice, s));
+      if (o.q) GB_CUDA(one(o.q, t.q, 8));
+      if (o.e_loc) GB_CUDA(one(o.e_loc, t.e_loc, 8));
+      if (o.iters) GB_CUDA(one(o.iters, t.iters, 4));
+      if (o.inner_iters) GB_CUDA(one(o.inner_iters, t.inner_iters, 4));
+      GB_CUDA(one(o.col_status, t.col_status, 4));
+      if (o.g_proj)
+        GB_CUDA(cudaMemcpy2DAsync(o.g_proj + 2 * ooff[c], 16 * (size_t)Po, t.g_proj + 2 * cb.soff[u][a],
+                                  16 * (size_t)Pt, 16 * (size_t)mc, K, cudaMemcpyDeviceToDevice, s));
+      ++fixed;
+    }
+    if (rest) left.push_back(i);
+  }
+  GB_CUDA(cudaStreamSynchronize(s));  // the temporaries are reused below
+  bool all = true;
+  for (const int i : left) {
+    int32_t f = 0;
+    const gb_status r = gb_correct_unconverged(mats[i], &params[i], &outs[i], workspace, workspace_bytes, stream, &f);
+    fixed += f;
+    if (r == GB_ENOCONV) {
+      all = false;
+    } else if (r != GB_OK) {
+      if (ncorrected) *ncorrected = fixed;
+      return r;
+    }
+  }
+  if (ncorrected) *ncorrected = fixed;
+  if (!all) return fail(GB_ENOCONV, "some columns still miss tol after the FP64 correction solves");
   return GB_OK;
 }
 
