@@ -337,7 +337,12 @@ __device__ __noinline__ void bc_pass_mma(const Args& a, Smem& sm, const InT* __r
     const int nunits = split ? 2 * ntile : ntile;
     for (int u = warp; u < nunits; u += NWARP) {
       const int ot = split ? u % ntile : u, role = split ? u / ntile : 2;  // 0 tri, 1 band, 2 both
-      const int mi = ot & 3, ni = ot >> 2;
+      // Warp w runs on sub-partition w mod 4.  The triangular part of m-tile
+      // mi takes 2 mi + 2 (FWD) or 8 - 2 mi (BWD) k-steps, so odd n-tiles run
+      // the m-tiles in reverse: every sub-partition then issues the same
+      // number of tensor instructions per step (10 k-steps of triangle per
+      // pair of n-tiles instead of 4 .. 16).
+      const int ni = ot >> 2, mi = (ni & 1) ? 3 - (ot & 3) : (ot & 3);
       float dh[4] = {0.f, 0.f, 0.f, 0.f}, dt[4] = {0.f, 0.f, 0.f, 0.f}, du[4] = {0.f, 0.f, 0.f, 0.f};
       float e[4] = {0.f, 0.f, 0.f, 0.f};
       if (role != 0 && s > 0) {  // band part against the previous output block
