@@ -218,9 +218,10 @@ def align_blocks(system: TBSystem) -> TBSystem:
     atom starts on a multiple of 4 (one whole 4x4 block of the BSR format).
 
     Atoms keep their order except that, wherever a 4-orbital atom would start
-    off a block boundary, the nearest following 1-orbital atoms move in front
-    of it until the boundary is reached (for the PPV chains: the first two
-    hydrogens of every odd monomer move ahead of its carbons).  H and S are
+    off a block boundary, 1-orbital atoms from the next few that follow move
+    in front of it until the boundary is reached, choosing those whose
+    couplings reach least far forward (for the PPV chains: two hydrogens of
+    every odd monomer move ahead of its carbons).  H and S are
     permuted as P H P^T, P S P^T, so the physics is unchanged; the locality of
     the numbering (and the band of S) is kept.
     """
@@ -228,22 +229,27 @@ def align_blocks(system: TBSystem) -> TBSystem:
     n_atoms = norb.shape[0]
     off = np.zeros(n_atoms + 1, dtype=np.int64)
     np.cumsum(norb, out=off[1:])
+    # furthest orbital each atom couples to (its first orbital's pattern row)
+    reach = system.col_idx[system.row_ptr[off[1:]] - 1] if n_atoms else np.zeros(0, np.int64)
     placed = np.zeros(n_atoms, dtype=bool)
     order = []
     pos = 0
-    nxt1 = 0  # scan pointer for the next unplaced 1-orbital atom
     for a in range(n_atoms):
         if placed[a]:
             continue
         if norb[a] == 4 and pos % 4 != 0:
-            nxt1 = max(nxt1, a + 1)
-            while pos % 4 != 0:
-                while nxt1 < n_atoms and (placed[nxt1] or norb[nxt1] != 1):
-                    nxt1 += 1
-                if nxt1 >= n_atoms:
-                    break
-                order.append(nxt1)
-                placed[nxt1] = True
+            # the next few unplaced 1-orbital atoms are candidates; those that
+            # reach least far forward move (the band of S grows least)
+            cand = []
+            b = a + 1
+            while b < n_atoms and len(cand) < 8:
+                if not placed[b] and norb[b] == 1:
+                    cand.append(b)
+                b += 1
+            need = (4 - pos % 4) % 4
+            for b in sorted(cand, key=lambda x: (reach[x], x))[:need]:
+                order.append(b)
+                placed[b] = True
                 pos += 1
         order.append(a)
         placed[a] = True
@@ -318,17 +324,21 @@ def uneven_chains(n_chains: int = 512, seed: int = 2, mono_range=(2, 50), shift_
 
 
 def uneven_batch(n_chains: int = 512, cols_per_chain: int = 2, seed: int = 2, eta: float = 0.02,
-                 tol: float = 1e-6, maxit: int = 16000):
+                 tol: float = 1e-6, maxit: int = 16000, align: bool = False):
     """The uneven-chain batch with sampled right-hand sides per chain.
 
     Chains as in ``uneven_chains`` (2..50 monomers, 32..256 shifts each on
     [-15, 10] eV + i*eta); each chain gets ``cols_per_chain`` distinct random
     unit right-hand sides (always including its first orbital), Fermi weights
-    and the common tolerance / iteration cap.  Returns (systems, problems).
+    and the common tolerance / iteration cap.  With ``align`` every chain is
+    renumbered by align_blocks (same draws otherwise).  Returns (systems,
+    problems).
     """
     rng = np.random.default_rng(seed + 7919)
     systems, problems = [], []
     for sysm, k in uneven_chains(n_chains, seed=seed):
+        if align:
+            sysm = align_blocks(sysm)
         z = shift_grid(-15.0, 10.0, k, eta)
         w_rho, w_edm = fermi_weights(z)
         extra = rng.choice(np.arange(1, sysm.n), size=cols_per_chain - 1, replace=False)
