@@ -203,6 +203,10 @@ typedef struct {
                             product (faster, but its rounding makes the
                             recursive residual estimate drift below the true
                             residual: pair it with gb_true_residual);
+                            bit 6: stop a column early once none of its open
+                            shifts has halved its best residual in the last
+                            3000 iterations (col_status 4 | 32; for use with
+                            the correction solves, which set it themselves);
                             other bits are ignored                           */
   int32_t seed_shift;    /* index of the seed shift; < 0: middle of the grid     */
   int32_t reserved;
@@ -227,7 +231,8 @@ typedef struct {
                            the exact factor solve                            */
   int32_t* col_status;  /* [nrhs] bit flags per column: 1 COCG breakdown, 2 S not
                            SPD, 4 a shift missed tol, 8 inner CG hit its cap,
-                           16 a bounded wait for a factor tile gave up        */
+                           16 a bounded wait for a factor tile gave up,
+                           32 stopped early as stalled (flags bit 6)          */
 } gb_outputs;
 
 /*

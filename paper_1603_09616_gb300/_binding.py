@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("GBGREEN_LIB") or os.path.join(_HERE, "libgbgreen.so")
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ENOTSPD, GB_EBREAKDOWN, GB_ENOCONV, GB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+FLAG_STALL = 64  # gb_solve_params.flags bit 6: stop stalled columns early
 GB_FP64, GB_MIXED = 0, 1
 _STATUS = {0: "GB_OK", -1: "GB_EINVAL", -2: "GB_ENOMEM", -3: "GB_ECUDA", -4: "GB_ENOTSPD", -5: "GB_EBREAKDOWN",
            -6: "GB_ENOCONV", -7: "GB_ETIMEOUT"}
@@ -352,10 +353,13 @@ def shifted_solve(mat: Matrix, z, cols, tol=1e-10, maxit=1000, prec="fp64", w_rh
     unconverged in the outputs.  With ``correct=True`` a GB_ENOCONV result
     (from the solve or the check) is passed to gb_correct_batched (one FP64
     re-solve of all failing columns, then seed switching for the rest);
-    ``corrected`` then holds the number of columns it fixed.
+    ``corrected`` then holds the number of columns it fixed, and the first
+    solve stops stalled columns early (flags bit 6).
     """
     import torch
 
+    if correct:
+        flags |= FLAG_STALL
     dev = torch.device("cuda", torch.cuda.current_device())
     keep = []
     p = _params(z, cols, tol, maxit, prec, w_rho, w_edm, inner_tol, panel, seed_shift, keep, flags)
@@ -575,6 +579,8 @@ def shifted_solve_batched(mats, problems, prec="mixed", panel=0, want_g=False, w
     """
     import torch
 
+    if correct:
+        flags |= FLAG_STALL
     dev = torch.device("cuda", torch.cuda.current_device())
     lib = load()
     nsys = len(mats)

@@ -102,6 +102,7 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
     sm.nc[tid] = 0;
     sm.st[tid] = 0;
     sm.nact[tid] = 0;
+    sm.nfresh[tid] = 0;
     sm.aprev[tid] = make_double2(1.0, 0.0);
     sm.bprev[tid] = make_double2(0.0, 0.0);
     sm.scl[tid] = 1.0;
@@ -353,6 +354,7 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
           hL[(size_t)(n + 1) * W + tid] = hL[(size_t)n * W + tid] + (s != 1.0 ? kRescaleExp : 0);
           sx.coef[tid] = shift_coef(sm.alpha[tid], sm.bprev[tid], sm.aprev[tid]);
           sm.nact[tid] = 0;
+          sm.nfresh[tid] = 0;
         }
       }
       __syncthreads();
@@ -410,6 +412,17 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
           resk[e] = sqrt(sm.rt2[cc] / ap2);
         } else {
           atomicAdd(&sm.nact[cc], 1);
+          if (a.stall > 0) {
+            // while the pair is open, resk holds its best squared residual so
+            // far and nk = -2 - (iteration of that best); both are rewritten
+            // when the column ends
+            const double r2 = sm.rt2[cc] / ap2, best = resk[e];
+            if (nk[e] == -1 || r2 < 0.25 * best) {
+              resk[e] = r2;
+              nk[e] = -2 - n;
+            }
+            if (n - (-2 - nk[e]) < a.stall) atomicAdd(&sm.nfresh[cc], 1);
+          }
         }
         const double s = sm.scl[cc];
         if (s != 1.0) {
@@ -433,6 +446,10 @@ __device__ void solve_panel(const Args& a, Smem& sm, PanelSmemExtra& sx, char* w
       if (sm.nact[tid] == 0) {
         sm.act[tid] = 0;
         sm.nc[tid] = n + 1;
+      } else if (a.stall > 0 && sm.nfresh[tid] == 0) {  // every open shift has stalled
+        sm.act[tid] = 0;
+        sm.nc[tid] = n + 1;
+        sm.st[tid] |= kStNoConv | kStStall;
       }
     }
     __syncthreads();

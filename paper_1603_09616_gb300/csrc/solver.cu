@@ -284,8 +284,11 @@ __global__ void __launch_bounds__(256, 4)
 // group at one address (a broadcast), its x rows by the group as contiguous
 // runs, and each value feeds PC complex columns from registers.  The groups
 // then add up through xor shuffles.  Requires x and y 16-byte aligned.
+// The kernel waits on loads (ncu at W = 8: long-scoreboard stalls dominate),
+// so it keeps one step in flight per lane at <= 64 registers, which lets 32
+// warps share an SM (two steps at 106 registers left 11 warps active).
 template <int CL>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 4)
     spmm_wide_kernel(const gbk::DevMat m, const float* __restrict__ A, const float4* __restrict__ x,
                      float4* __restrict__ y) {
   constexpr int G = 32 / CL;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(256, 2)
   };
   const int b1 = m.blk_ptr[I + 1];
   int b = m.blk_ptr[I] + g;
-  constexpr int U = 2;
+  constexpr int U = 1;
   int Jn[U];  // block columns one step ahead (one round trip per step)
 #pragma unroll
   for (int u = 0; u < U; ++u) Jn[u] = b + G * u < b1 ? __ldcs(m.blk_col + b + G * u) : 0;
@@ -739,10 +742,12 @@ namespace {
 // the FP64 path runs CG.  K Chebyshev steps reduce the preconditioned residual
 // below itol by the bound 2 sqrt(kappa) q^K (q = (sqrt(kappa) - 1) /
 // (sqrt(kappa) + 1)), with the Lanczos bounds widened by 2% on each side.
-constexpr int kFlagSmem = 2, kFlagCG = 4, kFlagCheb = 16, kFlagHpF32 = 32;
+constexpr int kFlagSmem = 2, kFlagCG = 4, kFlagCheb = 16, kFlagHpF32 = 32, kFlagStall = 64;
+constexpr int kStallWindow = 3000;  // iterations without halving the best residual
 void set_inner_method(const gb_matrix* m, const gb_solve_params* p, double itol, gbk::Args& a) {
   std::memset(&a, 0, sizeof a);
   a.hp_fp32 = (p->prec == GB_MIXED && (p->flags & kFlagHpF32)) ? 1 : 0;
+  a.stall = (p->flags & kFlagStall) ? kStallWindow : 0;
   if (!(p->flags & (kFlagCG | kFlagCheb)) && m->dm.bf_bw > 0) {
     a.inner_bchol = 1;  // exact: block-bidiagonal Cholesky factor solves
     // mixed: FP32 factor solves on TF32 tensor cores with a three-term split,
@@ -1732,7 +1737,7 @@ gb_status gb_correct_unconverged(const gb_matrix* m, const gb_solve_params* p, c
       q.prec = GB_FP64;
       q.seed_shift = kw;
       q.panel = 1;
-      q.flags = 0;
+      q.flags = kFlagStall;  // a stalled column stops early and tries the next seed
       q.inner_tol = 0.0;
       gb_outputs t{};
       t.ldos = out->ldos ? reinterpret_cast<double*>(wsb + L.o_ldos) : nullptr;
@@ -2228,6 +2233,7 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
       a.inner_bchol = im.inner_bchol;
       a.bc_levels = im.bc_levels;
       a.hp_fp32 = im.hp_fp32;
+      a.stall = im.stall;
       a.bc_bw_alloc = 63;  // the launch's shared memory is sized for any band
       a.cheb_K = im.cheb_K;
       a.cheb_c0 = im.cheb_c0;
@@ -2413,7 +2419,7 @@ gb_status corr_batch_plan(int32_t nsys, const gb_matrix* const* mats, const gb_s
     q.rhs_cols = cb->cols[u].data();
     q.prec = GB_FP64;
     q.panel = 1;
-    q.flags = 0;
+    q.flags = kFlagStall;  // a stalled column stops early and tries the next seed
     q.inner_tol = 0.0;
     cb->q[u] = q;
     const size_t K = q.nshift, n = q.nrhs;

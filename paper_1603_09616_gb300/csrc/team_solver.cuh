@@ -68,6 +68,8 @@ struct Args {
   // the iteration counts are produced.
   int full_hist;
   int hp_fp32;  // mixed path: H p as an unrefined FP32 product (flags bit 5)
+  int stall;    // > 0: stop a column whose unconverged shifts all went this many
+                // iterations without halving their best residual (flags bit 6)
   float cheb_c0;
   float cheb_A[48], cheb_B[48];
   double* ldos;
@@ -89,11 +91,12 @@ constexpr int kStNotSPD = 2;
 constexpr int kStNoConv = 4;
 constexpr int kStInner = 8;
 constexpr int kStTimeout = 16;  // a bounded wait for a staged factor tile gave up
+constexpr int kStStall = 32;    // stopped early: no shift of the column was improving
 
 struct Smem {
   RedSmem rs;
   int panel, Wp, flag, inner_count;
-  int j[WMAX], mc[WMAX], off[WMAX + 1], act[WMAX], nc[WMAX], nact[WMAX], st[WMAX];
+  int j[WMAX], mc[WMAX], off[WMAX + 1], act[WMAX], nc[WMAX], nact[WMAX], st[WMAX], nfresh[WMAX];
   double2 rho[WMAX], alpha[WMAX], beta[WMAX], aprev[WMAX], bprev[WMAX], gam[WMAX];
   double rt2[WMAX], scl[WMAX];
   double cg_rho[2 * WMAX], cg_un[2 * WMAX], cg_gg[2 * WMAX], cg_a[2 * WMAX], cg_b[2 * WMAX];

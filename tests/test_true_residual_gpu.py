@@ -79,3 +79,41 @@ def test_true_residual_check_drives_the_correction():
     for key in ("ldos", "rho", "edm", "q", "e_loc"):
         assert rel(fixed[key].cpu().numpy(), ref[key]) < 1e-6, key
     mat.close()
+
+
+def test_stalled_columns_stop_early_and_the_correction_fixes_them():
+    # Chain 331 of the uneven batch at eta 0.02 (N = 228, 115 shifts): its
+    # second column stalls above tol 1e-6 in the mixed path (near-gap shifts)
+    # and runs to maxit 16000; with flags bit 6 it stops once no open shift has
+    # halved its best residual for 3000 iterations (col_status 4 | 32).  The
+    # column that converges is untouched (same iterations, same outputs), and
+    # the correction then brings the stopped column to tol and to the oracle.
+    from synth import uneven_batch
+
+    torch.cuda.set_device(0)
+    systems, problems = uneven_batch(eta=0.02)
+    system, pr = systems[331], problems[331]
+    mat = gbg.Matrix(system)
+    maxit = pr["maxit"]
+    kw = dict(tol=pr["tol"], maxit=maxit, prec="mixed", w_rho=pr["w_rho"], w_edm=pr["w_edm"], panel=2, raise_on=())
+    full = gbg.shifted_solve(mat, pr["z"], pr["cols"], **kw)
+    early = gbg.shifted_solve(mat, pr["z"], pr["cols"], flags=gbg._binding.FLAG_STALL, **kw)
+    st = early["col_status"].cpu().numpy()
+    its_e = early["iters"].cpu().numpy()
+    its_f = full["iters"].cpu().numpy()
+    stalled = (st & 32) != 0
+    assert stalled.any() and not stalled.all()
+    assert np.all(st[stalled] & 4)
+    assert np.all(its_e[stalled] < maxit)
+    assert np.all(its_f[stalled] == maxit)  # running on did not reach tol either
+    ok = ~stalled
+    assert np.array_equal(its_e[ok], its_f[ok])
+    q_e, q_f = early["q"].cpu().numpy(), full["q"].cpu().numpy()
+    assert np.array_equal(q_e[ok], q_f[ok])
+    fixed = gbg.shifted_solve(mat, pr["z"], pr["cols"], correct=True, **kw)
+    assert fixed["status"] == 0, fixed["message"]
+    assert fixed["converged"].cpu().numpy().all()
+    ref = oracle.solve_outputs(system, pr["z"], pr["cols"], pr["w_rho"], pr["w_edm"])
+    for key in ("ldos", "rho", "edm", "q", "e_loc"):
+        assert rel(fixed[key].cpu().numpy(), ref[key]) < 1e-6, key
+    mat.close()
