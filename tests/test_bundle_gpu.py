@@ -74,9 +74,9 @@ def test_bundle_full_size_complex_symmetry(bundle):
     z = shift_grid(-6.0, 3.0, 4, 1.0)
     # sampled columns with many pattern neighbours among themselves: a few
     # seeds plus every fourth orbital of their pattern rows
-    seeds = random_columns(system.n, 6, seed=9)
+    seeds = random_columns(system.n, 2, seed=9)  # 69 columns, 1,164 symmetric pairs
     cols = np.unique(np.concatenate([system.row_cols(int(j))[::4] for j in seeds]).astype(np.int32))
-    out = gbg.shifted_solve(mat, z, cols, tol=1e-9, maxit=2000, prec="mixed", want_g=True)
+    out = gbg.shifted_solve(mat, z, cols, tol=1e-8, maxit=2000, prec="mixed", want_g=True)
     assert out["status"] == 0, out["message"]
     g = out["g_proj"].cpu().numpy()
     off = out["off"]

@@ -103,5 +103,13 @@ def test_surrogate_with_judge_on_fresh_bundle():
     assert rep["resolved"] >= rep["sample"] >= 1
     if not rep["fell_back"]:
         assert np.count_nonzero(np.isclose(qn, qf, rtol=0, atol=1e-9)) >= rep["resolved"]
+    # At the stated judge threshold 1e-3 this small network misses on most of
+    # the sample, so the judge must re-solve everything: the outputs are then
+    # the solver's own, whatever the network predicted.
+    q3, e3, rep3 = sg.infer_with_judge(sur, mf, fresh, z, w_rho, w_edm, tol=1e-6, maxit=4000, sample_frac=0.05,
+                                       threshold=1e-3)
+    assert rep3["fell_back"]
+    assert np.abs(q3.cpu().numpy() - qf).max() <= 1e-6 * np.abs(qf).max()
+    assert np.abs(e3.cpu().numpy() - ef).max() <= 1e-6 * np.abs(ef).max()
     for m in mats + [mf]:
         m.close()
