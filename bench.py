@@ -27,12 +27,14 @@ METRIC = "RHS·shift solves/s at rel err ≤1e-6 vs plain FP64 GPU; SpMM HBM GB/
 UNIT = "RHS·shift solves/s"
 NOMINAL_MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per launch from ncu captures of the current
-# kernels, for roofline.traffic; None until the changed kernel is captured
-# again.  spmm_quad_kernel<1> (FP32, one column) on the bundle Hamiltonian:
-SPMM_F32_W1_DRAM_BYTES = 333.958912e6
+# kernels, for roofline.traffic; None once a kernel changes, until it is
+# captured again.  spmm_quad_kernel<1> (FP32, one column) on the block-aligned
+# bundle Hamiltonian:
+SPMM_F32_W1_DRAM_BYTES = 271.619584e6
 # team_kernel<mixed> with the exact factor inner solve on the 1900-orbital
-# chain, bytes per column-iteration (scaled to a launch by its iterations):
-TEAM_MIXED_DRAM_BYTES_PER_COL_ITER = None
+# chain, bytes per column-iteration of a 60-iteration capture (84.54 GB over
+# 114,000 column-iterations), scaled to a launch by its column-iterations:
+TEAM_MIXED_DRAM_BYTES_PER_COL_ITER = 741.6e3
 
 
 def spmm_alg_bytes(info, v, W):

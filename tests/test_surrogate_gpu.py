@@ -108,6 +108,10 @@ def test_surrogate_with_judge_on_fresh_bundle():
     # the solver's own, whatever the network predicted.
     q3, e3, rep3 = sg.infer_with_judge(sur, mf, fresh, z, w_rho, w_edm, tol=1e-6, maxit=4000, sample_frac=0.05,
                                        threshold=1e-3)
+    # the share of sampled orbitals whose prediction the judge accepts at 1e-3
+    # (both outputs within 1e-3 of the solver); the fall-back rule needs 90 %
+    accepted = 1.0 - rep3["sample_miss_frac"]
+    assert 0.0 <= accepted < 0.9, accepted
     assert rep3["fell_back"]
     assert np.abs(q3.cpu().numpy() - qf).max() <= 1e-6 * np.abs(qf).max()
     assert np.abs(e3.cpu().numpy() - ef).max() <= 1e-6 * np.abs(ef).max()
