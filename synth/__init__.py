@@ -14,6 +14,8 @@ geometry here is a synthetic planar 14-atom phenylene-vinylene unit.
 from .tb import (  # noqa: F401
     TBSystem,
     align_blocks,
+    displace,
+    model_gradients,
     chain_4orb,
     ppv_chain,
     ppv_bundle,

@@ -272,6 +272,59 @@ def align_blocks(system: TBSystem) -> TBSystem:
     return out
 
 
+def _interatomic(system: TBSystem):
+    """Per CSR entry: row and column atoms, and the mask of entries between two
+    different atoms (the only entries that depend on positions; requires the
+    diagonal of S to sit at 1, i.e. the diagonal-dominance fix inactive)."""
+    if system.positions is None:
+        raise ValueError("the system has no atomic positions")
+    rows = np.repeat(np.arange(system.n), np.diff(system.row_ptr))
+    ai = system.orb_atom[rows].astype(np.int64)
+    aj = system.orb_atom[system.col_idx].astype(np.int64)
+    s_diag = system.s_val[rows == system.col_idx]
+    if not np.all(s_diag == 1.0):
+        raise ValueError("S's diagonal depends on positions for this system (diagonal-dominance fix active)")
+    return ai, aj, ai != aj
+
+
+def model_gradients(system: TBSystem):
+    """Gradients of H_ij and S_ij with respect to the position of the atom of
+    orbital i, per CSR entry ([3, nnz] each, nm^-1 units times the element).
+
+    Both decay rules are exponentials in d = r / r0, so dH_ij/dr = -H_ij / r0 and
+    dS_ij/dr = -S_ij / r0 along the unit vector from the column atom to the row
+    atom; entries within one atom do not depend on positions (zero).  These are
+    inputs of the force calculation, like H and S themselves.
+    """
+    ai, aj, inter = _interatomic(system)
+    d = system.positions[ai] - system.positions[aj]  # [nnz, 3]
+    r = np.linalg.norm(d, axis=1)
+    unit = np.zeros_like(d)
+    unit[inter] = d[inter] / r[inter, None]
+    gh = (-system.h_val / R0_NM)[:, None] * unit
+    gs = (-system.s_val / R0_NM)[:, None] * unit
+    gh[~inter] = 0.0
+    gs[~inter] = 0.0
+    return np.ascontiguousarray(gh.T), np.ascontiguousarray(gs.T)
+
+
+def displace(system: TBSystem, atom: int, delta) -> TBSystem:
+    """The same system with one atom moved by ``delta`` (nm): every element
+    between that atom and another is rescaled by exp(-(r' - r) / r0), the
+    decay rules' dependence on distance (the random factors stay)."""
+    ai, aj, inter = _interatomic(system)
+    pos = np.array(system.positions, dtype=np.float64, copy=True)
+    r_old = np.linalg.norm(pos[ai] - pos[aj], axis=1)
+    pos[atom] += np.asarray(delta, dtype=np.float64)
+    r_new = np.linalg.norm(pos[ai] - pos[aj], axis=1)
+    touched = inter & ((ai == atom) | (aj == atom))
+    f = np.ones(system.nnz)
+    f[touched] = np.exp(-(r_new[touched] - r_old[touched]) / R0_NM)
+    return TBSystem(n=system.n, row_ptr=system.row_ptr, col_idx=system.col_idx, h_val=system.h_val * f,
+                    s_val=system.s_val * f, orb_atom=system.orb_atom, name=system.name + "_displaced",
+                    positions=pos, atom_norb=system.atom_norb, meta=dict(system.meta))
+
+
 def ppv_bundle(
     n_side: int = 13,
     n_mono: int = 50,

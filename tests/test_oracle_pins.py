@@ -335,3 +335,63 @@ def test_fermi_level_two_site_half_filled_level_and_planted_spin():
     # a dropped spin factor would need the whole lower level: mu leaves it
     mu1 = of.fermi_level(z.real, ldos, 1.0, kT=0.05, spin=1.0)
     assert mu1 > lower + 0.2, mu1
+
+
+# ---------------------------------------------------------------- forces (f2)
+def _fd_case():
+    from oracle import forces as of
+
+    system = ppv_chain(2, seed=4)  # N = 76, 28 atoms, S diagonal at 1
+    mu, kT = 0.0, 0.1
+    rho, edm = of.eigen_density(system, mu, kT)
+    cols = np.arange(system.n)
+    from synth import model_gradients
+
+    gh, gs = model_gradients(system)
+    return system, mu, kT, of.pack(system, rho, cols), of.pack(system, edm, cols), cols, gh, gs
+
+
+def test_forces_are_minus_the_gradient_of_the_grand_potential():
+    # F_a = -dOmega/dR_a at fixed mu (central differences of the eigenvalue
+    # grand potential with the same random matrix factors), for the exact
+    # density and energy-density matrices of the eigen-decomposition
+    from oracle import forces as of
+    from synth import displace
+
+    system, mu, kT, rho, edm, cols, gh, gs = _fd_case()
+    F = of.forces(system, rho, edm, cols, gh, gs)
+    h = 1e-5
+    scale = np.abs(F).max()
+    for atom in (0, 5, 11, 20):
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            wp = of.grand_potential(displace(system, atom, e), mu, kT)
+            wm = of.grand_potential(displace(system, atom, -e), mu, kT)
+            fd = -(wp - wm) / (2 * h)
+            assert abs(F[atom, k] - fd) < 1e-6 * scale, (atom, k, F[atom, k], fd)
+
+
+def test_forces_sum_to_zero_and_exert_no_torque():
+    # two-center radial elements: every entry's gradients on its two atoms are
+    # opposite and along the bond, so sum_a F_a = 0 and sum_a R_a x F_a = 0
+    from oracle import forces as of
+
+    system, mu, kT, rho, edm, cols, gh, gs = _fd_case()
+    F = of.forces(system, rho, edm, cols, gh, gs)
+    scale = np.abs(F).max()
+    assert np.abs(F.sum(axis=0)).max() < 1e-11 * scale * len(F)
+    assert np.abs(np.cross(system.positions, F).sum(axis=0)).max() < 1e-10 * scale * len(F)
+
+
+def test_planted_dropped_energy_density_term_in_forces_is_caught():
+    # with S != I the P^E dS term matters: leaving it out misses the gradient
+    from oracle import forces as of
+    from synth import displace
+
+    system, mu, kT, rho, edm, cols, gh, gs = _fd_case()
+    F_bad = of.forces(system, rho, np.zeros_like(edm), cols, gh, gs)
+    h = 1e-5
+    e = np.array([h, 0.0, 0.0])
+    fd = -(of.grand_potential(displace(system, 5, e), mu, kT) - of.grand_potential(displace(system, 5, -e), mu, kT)) / (2 * h)
+    assert abs(F_bad[5, 0] - fd) > 1e-3 * abs(fd)
