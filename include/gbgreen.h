@@ -359,6 +359,37 @@ gb_status gb_fermi_density(const gb_matrix* m, const gb_solve_params* p, const d
 size_t gb_fermi_workspace_size(const gb_matrix* m, const gb_solve_params* p);
 
 /*
+ * gb_forces — atomic forces from the density and energy-density matrices of a
+ * finished solve of every orbital.
+ *
+ * The paper's molecular dynamics moves the atoms with forces from each step's
+ * electronic structure (Quantum molecular dynamics simulation).  For a
+ * non-orthogonal two-center tight-binding model at fixed chemical potential,
+ *   F_a = -Tr[rho dH/dR_a] + Tr[P^E dS/dR_a],
+ * with rho and P^E the solve's (or gb_fermi_density's) packed outputs; the
+ * traces run over both orders of every element (rho_ij from column j and
+ * rho_ji from column i), so they are exact for the matrices as computed.
+ *   p          the solve's parameters: rhs_cols must hold every orbital once
+ *   rho, edm   device [P], packed as gb_outputs.rho / edm of that solve
+ *   grad_h, grad_s  device [3][nnz]: per element of the CSR given to
+ *              gb_build_bsr (same order), the gradient of H_ij (S_ij) with
+ *              respect to the position of the atom of orbital i (row); the
+ *              gradient with respect to the other atom is its negative
+ *              (two-center elements); entries within one atom are ignored
+ *   atom_off   host [n_atoms + 1]: atom a owns orbitals atom_off[a] ..
+ *              atom_off[a+1]-1 (consecutive), atom_off[0] = 0, atom_off[n_atoms] = n
+ *   forces     device [n_atoms][3], overwritten
+ *   workspace  gb_forces_workspace_size(m, p, n_atoms) bytes, 256-byte aligned
+ * GB_EINVAL on a partial column set or bad atom ranges.  Synchronous.
+ */
+gb_status gb_forces(const gb_matrix* m, const gb_solve_params* p, const double* rho, const double* edm,
+                    const double* grad_h, const double* grad_s, const int64_t* atom_off, int32_t n_atoms,
+                    double* forces, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of workspace gb_forces needs (0: invalid arguments). */
+size_t gb_forces_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t n_atoms);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
  * The shifted equations of the Introduction for many independent structures

@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     Matrix,
     block_factor_to_host,
     fermi_density,
+    forces,
     bsr_to_host,
     load,
     pattern_offsets,

@@ -41,6 +41,8 @@ EXPORTED = (
     "gb_true_residual",
     "gb_fermi_density",
     "gb_correct_batched",
+    "gb_forces",
+    "gb_forces_workspace_size",
     "gb_correct_batched_workspace_size",
     "gb_fermi_workspace_size",
     "gb_true_residual_workspace_size",
@@ -141,6 +143,11 @@ def load() -> C.CDLL:
                                        C.c_void_p, C.POINTER(C.c_int32)]
     lib.gb_correct_batched_workspace_size.restype = C.c_size_t
     lib.gb_correct_batched_workspace_size.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_forces.restype = C.c_int
+    lib.gb_forces.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.gb_forces_workspace_size.restype = C.c_size_t
+    lib.gb_forces_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_int32]
     lib.gb_fermi_density.restype = C.c_int
     lib.gb_fermi_density.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_double,
                                      C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(Outputs), C.c_void_p,
@@ -473,6 +480,35 @@ def fermi_density(mat: Matrix, z, cols, solved: dict, n_electrons: float, kT: fl
     res["mu"] = float(mu.value)
     res["off"] = solved["off"]
     return res
+
+
+def forces(mat: Matrix, cols, rho, edm, grad_h, grad_s, atom_off, stream=None):
+    """Atomic forces [n_atoms, 3] (gb_forces) from packed rho / P^E (device
+    tensors of a solve of every orbital in ``cols``), per-element gradients
+    grad_h, grad_s [3, nnz] (CSR order, numpy or device tensors) and the
+    orbital ranges of the atoms ``atom_off`` [n_atoms + 1]."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    z = np.zeros(1, dtype=np.complex128) + 1j
+    p = _params(z, cols, 1e-10, 1, "fp64", None, None, 0.0, 0, -1, keep)
+    ao = np.ascontiguousarray(atom_off, dtype=np.int64)
+    n_atoms = len(ao) - 1
+    lib = load()
+    need = lib.gb_forces_workspace_size(mat.handle, C.byref(p), n_atoms)
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    gh = torch.as_tensor(np.ascontiguousarray(grad_h) if isinstance(grad_h, np.ndarray) else grad_h, **f64).contiguous()
+    gs = torch.as_tensor(np.ascontiguousarray(grad_s) if isinstance(grad_s, np.ndarray) else grad_s, **f64).contiguous()
+    out = torch.empty((n_atoms, 3), **f64)
+    _check(lib.gb_forces(mat.handle, C.byref(p), C.c_void_p(rho.data_ptr()), C.c_void_p(edm.data_ptr()),
+                         C.c_void_p(gh.data_ptr()), C.c_void_p(gs.data_ptr()), _ptr(ao), n_atoms,
+                         C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()),
+                         _stream_handle(stream)))
+    return out
 
 
 def true_residual(mat: Matrix, z, cols, verify, tol=1e-10, maxit=1000, prec="fp64", inner_tol=0.0, panel=0,

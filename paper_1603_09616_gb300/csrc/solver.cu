@@ -2587,3 +2587,136 @@ gb_status gb_correct_batched(int32_t nsys, const gb_matrix* const* mats, const g
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ atomic forces
+// F_a = -Tr[rho dH/dR_a] + Tr[P^E dS/dR_a] (Quantum molecular dynamics
+// simulation: the forces of each MD step) from the rho / P^E of a solve of
+// every orbital.  For two-center elements the gradient of entry (j, i) with
+// respect to the atom of row j is grad[:, e] (e its CSR position) and with
+// respect to the atom of i its negative; the element (i, j) is the same
+// function, so the trace over both orders gives
+//   F_a = -sum_{j in a} sum_{i in R_j, atom(i) != a} ((rho_ij + rho_ji) gH_e - (P^E_ij + P^E_ji) gS_e),
+// rho_ij read from column j of the packed output and rho_ji from column i (the
+// two differ by the solve's rounding; the sum keeps the trace exact for the
+// matrix as computed).  One warp per atom; the lanes take the entries of its
+// orbitals' pattern rows and reduce in a fixed order (deterministic).
+namespace {
+
+__global__ void __launch_bounds__(256) forces_kernel(const gbk::DevMat m, const int* __restrict__ atom_off,
+                                                     const int* __restrict__ orb_atom, const int* __restrict__ col_of,
+                                                     const long long* __restrict__ off,
+                                                     const long long* __restrict__ tpos, const double* __restrict__ rho,
+                                                     const double* __restrict__ edm, const double* __restrict__ gh,
+                                                     const double* __restrict__ gs, long long nnz, int n_atoms,
+                                                     double* __restrict__ F) {
+  const int a = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (a >= n_atoms) return;  // uniform per warp
+  const int lane = threadIdx.x & 31;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  for (int j = atom_off[a]; j < atom_off[a + 1]; ++j) {
+    const int c = col_of[j], e0 = m.row_ptr[j], e1 = m.row_ptr[j + 1];
+    const long long base = off[c] - e0;  // packed index of entry e in column j: base + e
+    for (int e = e0 + lane; e < e1; e += 32) {
+      if (orb_atom[m.col_idx[e]] == a) continue;
+      const long long o = tpos[e];  // the same element in column i
+      const double r = rho[base + e] + rho[o], q = edm[base + e] + edm[o];
+      fx = fma(q, gs[e], fma(-r, gh[e], fx));
+      fy = fma(q, gs[nnz + e], fma(-r, gh[nnz + e], fy));
+      fz = fma(q, gs[2 * nnz + e], fma(-r, gh[2 * nnz + e], fz));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+  }
+  if (lane == 0) {
+    F[3 * a] = fx;
+    F[3 * a + 1] = fy;
+    F[3 * a + 2] = fz;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_forces_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t n_atoms) {
+  clear_error();
+  if (!m || !p || p->nrhs < 1 || n_atoms < 1) {
+    fail(GB_EINVAL, "NULL argument, no columns or no atoms");
+    return 0;
+  }
+  return align256(4 * ((size_t)n_atoms + 1)) + 2 * align256(4 * (size_t)m->n) +
+         align256(8 * ((size_t)p->nrhs + 1)) + align256(8 * (size_t)m->nnz) + 256;
+}
+
+gb_status gb_forces(const gb_matrix* m, const gb_solve_params* p, const double* rho, const double* edm,
+                    const double* grad_h, const double* grad_s, const int64_t* atom_off, int32_t n_atoms,
+                    double* forces, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!m || !p || !rho || !edm || !grad_h || !grad_s || !atom_off || !forces) return fail(GB_EINVAL, "NULL argument");
+  const int n = (int)m->n, nrhs = p->nrhs;
+  if (n_atoms < 1 || atom_off[0] != 0 || atom_off[n_atoms] != n)
+    return fail(GB_EINVAL, "atom_off must run from 0 to n over n_atoms atoms");
+  for (int a = 0; a < n_atoms; ++a)
+    if (atom_off[a + 1] <= atom_off[a]) return fail(GB_EINVAL, "atom %d has no orbitals", a);
+  if (nrhs != n || !p->rhs_cols) return fail(GB_EINVAL, "forces need every orbital solved (nrhs = n)");
+  std::vector<int> col_of(n, -1), orb_atom(n), aoff(n_atoms + 1);
+  for (int c = 0; c < nrhs; ++c) {
+    const int j = p->rhs_cols[c];
+    if (j < 0 || j >= n || col_of[j] >= 0) return fail(GB_EINVAL, "rhs_cols must hold every orbital once");
+    col_of[j] = c;
+  }
+  for (int a = 0; a < n_atoms; ++a) {
+    aoff[a] = (int)atom_off[a];
+    for (int64_t j = atom_off[a]; j < atom_off[a + 1]; ++j) orb_atom[j] = a;
+  }
+  aoff[n_atoms] = n;
+  const size_t need = gb_forces_workspace_size(m, p, n_atoms);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < need) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+  std::vector<long long> off(nrhs + 1, 0);
+  for (int c = 0; c < nrhs; ++c) {
+    const int j = p->rhs_cols[c];
+    off[c + 1] = off[c] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+  }
+  // packed index of every CSR element's transpose: entry e = (row j, column i)
+  // lies in column j; the element (i, j) lies in column i at the position of j in R_i
+  const std::vector<int64_t>& rp = m->h_row_ptr;
+  std::vector<int32_t> ci(m->nnz);
+  GB_CUDA(cudaMemcpy(ci.data(), m->dm.col_idx, 4 * (size_t)m->nnz, cudaMemcpyDeviceToHost));
+  std::vector<long long> tp(m->nnz);
+  for (int j = 0; j < n; ++j)
+    for (int64_t e = rp[j]; e < rp[j + 1]; ++e) {
+      const int i = ci[e];
+      const int32_t* r0 = ci.data() + rp[i];
+      const int32_t* r1 = ci.data() + rp[i + 1];
+      const int32_t* hit = std::lower_bound(r0, r1, j);
+      if (hit == r1 || *hit != j) return fail(GB_EINVAL, "the pattern is not symmetric");
+      tp[e] = off[col_of[i]] + (hit - r0);
+    }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  int* d_aoff = reinterpret_cast<int*>(w);
+  int* d_atom = reinterpret_cast<int*>(w + align256(4 * ((size_t)n_atoms + 1)));
+  int* d_col = reinterpret_cast<int*>(w + align256(4 * ((size_t)n_atoms + 1)) + align256(4 * (size_t)n));
+  long long* d_off =
+      reinterpret_cast<long long*>(w + align256(4 * ((size_t)n_atoms + 1)) + 2 * align256(4 * (size_t)n));
+  GB_CUDA(cudaMemcpyAsync(d_aoff, aoff.data(), 4 * ((size_t)n_atoms + 1), cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_atom, orb_atom.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_col, col_of.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_off, off.data(), 8 * ((size_t)nrhs + 1), cudaMemcpyHostToDevice, s));
+  long long* d_tp = reinterpret_cast<long long*>(reinterpret_cast<char*>(d_off) + align256(8 * ((size_t)nrhs + 1)));
+  GB_CUDA(cudaMemcpyAsync(d_tp, tp.data(), 8 * (size_t)m->nnz, cudaMemcpyHostToDevice, s));
+  const unsigned blocks = (unsigned)(((long long)n_atoms * 32 + 255) / 256);
+  forces_kernel<<<blocks, 256, 0, s>>>(m->dm, d_aoff, d_atom, d_col, d_off, d_tp, rho, edm, grad_h, grad_s,
+                                       (long long)m->nnz, n_atoms, forces);
+  GB_CUDA(cudaGetLastError());
+  GB_CUDA(cudaStreamSynchronize(s));  // the host staging vectors are this call's locals
+  return GB_OK;
+}
+
+}  // extern "C"
