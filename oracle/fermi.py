@@ -91,3 +91,34 @@ def fermi_outputs(system, z, n_electrons, kT, spin=2.0):
     out["mu"] = mu
     out["g_proj"] = g
     return out
+
+
+def sinv_terms(system, cols):
+    """S^-1 and S^-1 H S^-1 on the pattern, packed like rho (dense inverse)."""
+    from .forces import pack
+
+    H, S = system.dense()
+    Sinv = np.linalg.inv(S)
+    return pack(system, Sinv, cols), pack(system, Sinv @ H @ Sinv, cols)
+
+
+def outputs_with_sinv(system, z, cols, c_rho, c_edm, a_rho, b_edm, c_shs):
+    """Shifted-solve reductions with weights (c_rho, c_edm), plus a_rho S^-1 in
+    rho and b_edm S^-1 + c_shs S^-1 H S^-1 in P^E (the terms of a pole
+    expansion of the Fermi function that are not resolvents); q and e_loc
+    from the completed rho."""
+    cols = np.asarray(cols)
+    H, S = system.dense()
+    X = green_columns(H, S, np.asarray(z), cols)
+    g = project_columns(system, X, cols)
+    out = reduce_outputs(system, g, cols, c_rho, c_edm)
+    si, shs = sinv_terms(system, cols)
+    out["rho"] = out["rho"] + a_rho * si
+    out["edm"] = out["edm"] + b_edm * si + c_shs * shs
+    off = out["off"]
+    for c, j in enumerate(cols):
+        lo, hi = int(system.row_ptr[j]), int(system.row_ptr[j + 1])
+        r = out["rho"][off[c] : off[c + 1]]
+        out["q"][c] = np.sum(r * system.s_val[lo:hi])
+        out["e_loc"][c] = np.sum(r * system.h_val[lo:hi])
+    return out

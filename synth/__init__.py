@@ -16,6 +16,7 @@ from .tb import (  # noqa: F401
     align_blocks,
     displace,
     model_gradients,
+    pole_weights,
     chain_4orb,
     ppv_chain,
     ppv_bundle,

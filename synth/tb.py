@@ -422,6 +422,41 @@ def fermi_weights(z: np.ndarray, mu: float = 0.0, kT: float = 0.1):
     return c_rho, c_edm
 
 
+def pole_weights(mu: float = 0.0, kT: float = 0.1, n_poles: int = 40, spin: float = 2.0):
+    """Shifts and weights of a pole expansion of the Fermi function (a complex
+    shift set for the same solve, instead of the real-axis grid).
+
+    The continued fraction of tanh truncated at depth 2 n_poles gives
+    f(x) = 1 / (1 + e^x) ~= 1/2 + sum_p R_p [1 / (x - i a_p) + 1 / (x + i a_p)]
+    with a_p = 1 / b_p and R_p = -v_p,1^2 / (4 b_p^2) from the positive
+    eigenvalues b_p (eigenvectors v_p) of the symmetric tridiagonal matrix with
+    off-diagonal 1 / (2 sqrt((2m - 1)(2m + 1))), m = 1 .. 2 n_poles - 1.  With
+    x = (eps - mu) / kT the poles are w_p = mu + i kT a_p (the first at
+    i pi kT) and, for the generalized problem,
+      rho / s = 1/2 S^-1 - 2 kT sum_p R_p Re G(w_p),
+      P^E / s = 1/2 S^-1 H S^-1 + 2 kT (sum_p R_p) S^-1 - 2 kT sum_p R_p Re(w_p G(w_p)).
+    Returns (z, c_rho, c_edm, a_rho, b_edm, c_edm_shs): the shifts w_p, the
+    library weights with sum_k Im(c_k G(z_k)) equal to the pole sums, and the
+    coefficients of S^-1 in rho, of S^-1 in P^E and of S^-1 H S^-1 in P^E.
+    """
+    m2 = 2 * n_poles
+    B = np.zeros((m2, m2))
+    for m in range(1, m2):
+        B[m - 1, m] = B[m, m - 1] = 1.0 / (2.0 * np.sqrt((2 * m - 1) * (2 * m + 1)))
+    b, V = np.linalg.eigh(B)
+    pos = b > 0
+    bp, v1 = b[pos], V[0, pos]
+    a = 1.0 / bp
+    R = -(v1 ** 2) / (4.0 * bp ** 2)
+    order = np.argsort(a)
+    a, R = a[order], R[order]
+    z = mu + 1j * kT * a
+    c_rho = (-2.0 * kT * spin * R) * 1j
+    c_edm = (-2.0 * kT * spin * R) * 1j * z
+    return z, c_rho.astype(np.complex128), c_edm.astype(np.complex128), 0.5 * spin, 2.0 * kT * spin * R.sum(), \
+        0.5 * spin
+
+
 def random_columns(n: int, count: int, seed: int = 7) -> np.ndarray:
     """``count`` distinct orbital indices in [0, n), sorted."""
     rng = np.random.default_rng(seed)

@@ -395,3 +395,41 @@ def test_planted_dropped_energy_density_term_in_forces_is_caught():
     e = np.array([h, 0.0, 0.0])
     fd = -(of.grand_potential(displace(system, 5, e), mu, kT) - of.grand_potential(displace(system, 5, -e), mu, kT)) / (2 * h)
     assert abs(F_bad[5, 0] - fd) > 1e-3 * abs(fd)
+
+
+# ---------------------------------------------------------------- pole expansion (f3)
+def test_pole_expansion_reproduces_the_fermi_function():
+    from oracle import fermi as of
+    from synth import pole_weights
+
+    kT, spin = 0.1, 2.0
+    z, c, ce, a, b, cs = pole_weights(mu=0.3, kT=kT, n_poles=40, spin=spin)
+    R = (c / (-2.0 * kT * spin * 1j)).real
+    ap = z.imag / kT
+    assert np.allclose(z.real, 0.3) and ap.min() > 3.14159 and ap.min() < 3.1416  # first pole at i pi kT
+    x = np.linspace(-400, 400, 200001)
+    fx = 0.5 + (R[None, :] * (1 / (x[:, None] - 1j * ap) + 1 / (x[:, None] + 1j * ap))).sum(1).real
+    assert np.abs(fx - of.fermi(x)).max() < 1e-13
+
+
+def test_pole_expansion_gives_the_finite_temperature_density_matrices():
+    # rho = s f(S^-1 H) S^-1 and P^E = S^-1 H rho, exactly (eigen-decomposition),
+    # from 40 resolvents far from the real axis plus the S^-1 terms
+    from oracle import fermi as of
+    from oracle import forces as ofo
+    from synth import pole_weights
+
+    system = ppv_chain(2, seed=4)
+    mu, kT = 0.2, 0.1
+    cols = np.arange(system.n)
+    z, c, ce, a, b, cs = pole_weights(mu=mu, kT=kT, n_poles=40)
+    out = of.outputs_with_sinv(system, z, cols, c, ce, a, b, cs)
+    rho_e, edm_e = ofo.eigen_density(system, mu, kT)
+    rho_p, edm_p = ofo.pack(system, rho_e, cols), ofo.pack(system, edm_e, cols)
+    assert np.abs(out["rho"] - rho_p).max() < 1e-11 * np.abs(rho_p).max()
+    assert np.abs(out["edm"] - edm_p).max() < 1e-11 * np.abs(edm_p).max()
+    H, S = system.dense()
+    assert abs(out["q"].sum() - np.trace(rho_e @ S)) < 1e-10 * system.n
+    # planted: without the S^-1 H S^-1 term P^E is wrong
+    si, shs = of.sinv_terms(system, cols)
+    assert np.abs(out["edm"] - cs * shs - edm_p).max() > 1e-2 * np.abs(edm_p).max()
