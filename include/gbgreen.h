@@ -390,6 +390,31 @@ gb_status gb_forces(const gb_matrix* m, const gb_solve_params* p, const double* 
 size_t gb_forces_workspace_size(const gb_matrix* m, const gb_solve_params* p, int32_t n_atoms);
 
 /*
+ * gb_add_sinv_terms — the non-resolvent terms of a pole expansion of the Fermi
+ * function, added to a finished solve's outputs.
+ *
+ * The paper leaves the choice of shifts open (Introduction).  Expanding the
+ * Fermi function in poles w_p off the real axis, f(x) ~ 1/2 + sum_p R_p
+ * [1/(x - i a_p) + c.c.] (x = (eps - mu)/kT), makes rho and P^E sums of
+ * resolvents G(w_p), which the solve forms from weights c_k, plus
+ *   rho += a_rho S^-1,    P^E += b_edm S^-1 + c_shs S^-1 H S^-1
+ * on the pattern, which no resolvent gives.  This call adds those terms for
+ * the solve's columns (FP64 factor solves; needs S's half-bandwidth <= 63) and
+ * recomputes q and e_loc from the completed rho.
+ *   p        the solve's parameters (its rhs_cols)
+ *   out      its rho / edm are updated in place (either may be NULL), q and
+ *            e_loc overwritten when present
+ *   workspace gb_add_sinv_terms_workspace_size(m, p) bytes, 256-byte aligned
+ * GB_EINVAL without a factor, GB_ETIMEOUT if a bounded wait of a factor pass
+ * gave up.  Synchronous.
+ */
+gb_status gb_add_sinv_terms(const gb_matrix* m, const gb_solve_params* p, double a_rho, double b_edm, double c_shs,
+                            const gb_outputs* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of workspace gb_add_sinv_terms needs (0: invalid arguments). */
+size_t gb_add_sinv_terms_workspace_size(const gb_matrix* m, const gb_solve_params* p);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
  * The shifted equations of the Introduction for many independent structures

@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     GBError,
     Matrix,
     block_factor_to_host,
+    add_sinv_terms,
     fermi_density,
     forces,
     bsr_to_host,

@@ -42,6 +42,8 @@ EXPORTED = (
     "gb_fermi_density",
     "gb_correct_batched",
     "gb_forces",
+    "gb_add_sinv_terms",
+    "gb_add_sinv_terms_workspace_size",
     "gb_forces_workspace_size",
     "gb_correct_batched_workspace_size",
     "gb_fermi_workspace_size",
@@ -143,6 +145,11 @@ def load() -> C.CDLL:
                                        C.c_void_p, C.POINTER(C.c_int32)]
     lib.gb_correct_batched_workspace_size.restype = C.c_size_t
     lib.gb_correct_batched_workspace_size.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gb_add_sinv_terms.restype = C.c_int
+    lib.gb_add_sinv_terms.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_double, C.c_double, C.c_double,
+                                      C.POINTER(Outputs), C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.gb_add_sinv_terms_workspace_size.restype = C.c_size_t
+    lib.gb_add_sinv_terms_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
     lib.gb_forces.restype = C.c_int
     lib.gb_forces.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -480,6 +487,30 @@ def fermi_density(mat: Matrix, z, cols, solved: dict, n_electrons: float, kT: fl
     res["mu"] = float(mu.value)
     res["off"] = solved["off"]
     return res
+
+
+def add_sinv_terms(mat: Matrix, cols, solved: dict, a_rho: float, b_edm: float, c_shs: float, stream=None) -> dict:
+    """Add a_rho S^-1 to rho and b_edm S^-1 + c_shs S^-1 H S^-1 to P^E on the
+    pattern of ``cols`` (the outputs of :func:`shifted_solve`, updated in place;
+    q and e_loc recomputed): gb_add_sinv_terms."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    z = np.zeros(1, dtype=np.complex128) + 1j
+    p = _params(z, cols, 1e-10, 1, "fp64", None, None, 0.0, 0, -1, keep)
+    lib = load()
+    need = lib.gb_add_sinv_terms_workspace_size(mat.handle, C.byref(p))
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    o = Outputs()
+    for f, _ in Outputs._fields_:
+        t = solved.get(f) if f in ("rho", "edm", "q", "e_loc") else None
+        setattr(o, f, C.c_void_p(t.data_ptr()) if t is not None else None)
+    _check(lib.gb_add_sinv_terms(mat.handle, C.byref(p), float(a_rho), float(b_edm), float(c_shs), C.byref(o),
+                                 C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), _stream_handle(stream)))
+    return solved
 
 
 def forces(mat: Matrix, cols, rho, edm, grad_h, grad_s, atom_off, stream=None):

@@ -2720,3 +2720,130 @@ gb_status gb_forces(const gb_matrix* m, const gb_solve_params* p, const double* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ S^-1 terms
+// A pole expansion of the Fermi function leaves, besides the resolvents the
+// shifted solve forms, multiples of S^-1 (in rho and P^E) and of S^-1 H S^-1
+// (in P^E).  gb_add_sinv_terms adds them on the pattern: one team per chunk of
+// 32 columns forms X = S^-1 E (E the unit columns), Y = H X and Z = S^-1 Y with
+// the FP64 factor, then rho_ij += a X_ij and P^E_ij += b X_ij + c Z_ij on the
+// pattern rows of each column; q and E are then recomputed from rho.
+namespace {
+
+__global__ void __launch_bounds__(gbk::TPB, 1)
+    sinv_terms_kernel(const __grid_constant__ gbk::Args a, const int* __restrict__ cols,
+                      const long long* __restrict__ off, int nrhs, double a_rho, double b_edm, double c_shs,
+                      double* __restrict__ rho, double* __restrict__ edm, char* __restrict__ scratch,
+                      size_t panel_bytes, int* __restrict__ status) {
+  __shared__ gbk::Smem sm;
+  extern __shared__ __align__(16) char dyn_smem[];
+  gbk::team_init(sm, dyn_smem);
+  constexpr int W = 32;
+  const int c0 = blockIdx.x * W, tid = threadIdx.x;
+  const int N4 = 4 * a.m.nb;
+  char* base = scratch + (size_t)blockIdx.x * 5 * panel_bytes;
+  double2* E = reinterpret_cast<double2*>(base);
+  double2* X = reinterpret_cast<double2*>(base + panel_bytes);
+  double2* Z = reinterpret_cast<double2*>(base + 2 * panel_bytes);
+  double2* t1 = reinterpret_cast<double2*>(base + 3 * panel_bytes);
+  double2* t2 = reinterpret_cast<double2*>(base + 4 * panel_bytes);
+  if (tid < gbk::WMAX) sm.act[tid] = (tid < W && c0 + tid < nrhs) ? 1 : 0;
+  if (tid == 0) sm.inner_count = 0;
+  for (size_t e = tid; e < (size_t)N4 * W; e += gbk::TPB) {
+    const int row = (int)(e / W), l = (int)(e - (size_t)row * W);
+    E[e] = make_double2((c0 + l < nrhs && cols[c0 + l] == row) ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  gbk::bc_solve<double>(a, sm, E, X, t1, t2, dyn_smem);  // X = S^-1 E (ends with a barrier)
+  for (int it = tid; it < a.m.nb * W; it += gbk::TPB) {  // E <- H X
+    const int I = it / W, l = it - I * W;
+    double2 acc[4];
+    gbk::bsr_row_d(a.m, a.m.hb, X, W, l, I, acc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) E[(size_t)(4 * I + r) * W + l] = acc[r];
+  }
+  __syncthreads();
+  gbk::bc_solve<double>(a, sm, E, Z, t1, t2, dyn_smem);  // Z = S^-1 H S^-1 E
+  for (int l = 0; l < W && c0 + l < nrhs; ++l) {
+    const int c = c0 + l, j = cols[c], e0 = a.m.row_ptr[j], len = a.m.row_ptr[j + 1] - e0;
+    for (int t = tid; t < len; t += gbk::TPB) {
+      const int i = a.m.col_idx[e0 + t];
+      const double x = X[(size_t)i * W + l].x, zv = Z[(size_t)i * W + l].x;
+      const long long o = off[c] + t;
+      if (rho) rho[o] += a_rho * x;
+      if (edm) edm[o] += b_edm * x + c_shs * zv;
+    }
+  }
+  if (tid == 0 && sm.bc_fail) atomicOr(status, gbk::kStTimeout);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_add_sinv_terms_workspace_size(const gb_matrix* m, const gb_solve_params* p) {
+  clear_error();
+  if (!m || !p || p->nrhs < 1) {
+    fail(GB_EINVAL, "NULL argument or no columns");
+    return 0;
+  }
+  const size_t chunks = ((size_t)p->nrhs + 31) / 32, panel = align256(16 * 4 * (size_t)m->nb * 32);
+  return align256(4 * (size_t)p->nrhs) + align256(8 * ((size_t)p->nrhs + 1)) + 256 + chunks * 5 * panel;
+}
+
+gb_status gb_add_sinv_terms(const gb_matrix* m, const gb_solve_params* p, double a_rho, double b_edm, double c_shs,
+                            const gb_outputs* out, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!m || !p || !out || !p->rhs_cols || p->nrhs < 1) return fail(GB_EINVAL, "NULL argument or no columns");
+  if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
+  const int nrhs = p->nrhs;
+  for (int c = 0; c < nrhs; ++c)
+    if (p->rhs_cols[c] < 0 || p->rhs_cols[c] >= m->n) return fail(GB_EINVAL, "rhs_cols[%d] out of range", c);
+  const size_t need = gb_add_sinv_terms_workspace_size(m, p);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < need) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device differs from the matrix's device");
+  std::vector<long long> off(nrhs + 1, 0);
+  for (int c = 0; c < nrhs; ++c) {
+    const int j = p->rhs_cols[c];
+    off[c + 1] = off[c] + (m->h_row_ptr[j + 1] - m->h_row_ptr[j]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  int* d_cols = reinterpret_cast<int*>(w);
+  long long* d_off = reinterpret_cast<long long*>(w + align256(4 * (size_t)nrhs));
+  int* d_st = reinterpret_cast<int*>(w + align256(4 * (size_t)nrhs) + align256(8 * ((size_t)nrhs + 1)));
+  char* scratch = w + align256(4 * (size_t)nrhs) + align256(8 * ((size_t)nrhs + 1)) + 256;
+  const size_t panel = align256(16 * 4 * (size_t)m->nb * 32);
+  GB_CUDA(cudaMemcpyAsync(d_cols, p->rhs_cols, 4 * (size_t)nrhs, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemcpyAsync(d_off, off.data(), 8 * ((size_t)nrhs + 1), cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemsetAsync(d_st, 0, sizeof(int), s));
+  GB_CUDA(cudaMemsetAsync(scratch, 0, (size_t)((nrhs + 31) / 32) * 5 * panel, s));
+  gbk::Args a;
+  std::memset(&a, 0, sizeof a);
+  a.m = m->dm;
+  a.W = 32;
+  a.inner_bchol = 1;
+  a.bc_bw_alloc = m->dm.bf_bw;
+  const size_t dyn = gbk::dyn_layout(true, 32, true, 0, m->dm.bf_bw).bytes;
+  GB_CUDA(cudaFuncSetAttribute(sinv_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  const unsigned chunks = (unsigned)((nrhs + 31) / 32);
+  sinv_terms_kernel<<<chunks, gbk::TPB, dyn, s>>>(a, d_cols, d_off, nrhs, a_rho, b_edm, c_shs, out->rho, out->edm,
+                                                   scratch, panel, d_st);
+  GB_CUDA(cudaGetLastError());
+  if (out->rho && (out->q || out->e_loc)) {
+    local_sums_kernel<<<(unsigned)((nrhs + 255) / 256), 256, 0, s>>>(m->dm, d_cols, d_off, nrhs, out->rho, out->q,
+                                                                     out->e_loc);
+    GB_CUDA(cudaGetLastError());
+  }
+  int hst = 0;
+  GB_CUDA(cudaMemcpyAsync(&hst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  if (hst & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
+  return GB_OK;
+}
+
+}  // extern "C"
