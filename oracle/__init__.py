@@ -15,7 +15,7 @@ sparsity pattern, local charge and local energy).  The paper itself notes that
 a direct O(N^3) solver is the numerically exact complement of the order-N
 solver (Introduction), which is why a direct solve serves as the reference.
 """
-from . import fermi, forces  # noqa: F401
+from . import fermi, forces, wavepacket  # noqa: F401
 from .green import (  # noqa: F401
     green_columns,
     green_columns_sparse,

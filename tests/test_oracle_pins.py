@@ -433,3 +433,35 @@ def test_pole_expansion_gives_the_finite_temperature_density_matrices():
     # planted: without the S^-1 H S^-1 term P^E is wrong
     si, shs = of.sinv_terms(system, cols)
     assert np.abs(out["edm"] - cs * shs - edm_p).max() > 1e-2 * np.abs(edm_p).max()
+
+
+# ---------------------------------------------------------------- wavepacket (f4)
+def test_wavepacket_spectral_sum_equals_the_matrix_exponential():
+    import scipy.linalg as sla
+
+    from oracle import wavepacket as ow
+
+    system = ppv_chain(2, seed=6)
+    H, S = system.dense()
+    rng = np.random.default_rng(3)
+    c0 = rng.standard_normal((system.n, 3)) + 1j * rng.standard_normal((system.n, 3))
+    t = 1.7
+    ref = sla.expm(-1j * t * np.linalg.solve(S, H)) @ c0
+    got = ow.propagate(system, c0, t)
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+    # the S-norm is conserved, and an eigenstate only turns its phase
+    assert np.allclose(ow.s_norm(system, got), ow.s_norm(system, c0), rtol=1e-12)
+    y, lam = ow.homo(system, system.n)
+    yt = ow.propagate(system, y[:, None], t)[:, 0]
+    assert np.abs(yt - np.exp(-1j * lam * t) * y).max() < 1e-12 * np.abs(y).max()
+
+
+def test_wavepacket_two_site_rabi_oscillation():
+    # S = I, H = [[e, v], [v, e]]: c(0) = e_1 gives exp(-i e t) (cos vt, -i sin vt)
+    from oracle import wavepacket as ow
+
+    e, v, t = 0.3, -1.1, 0.9
+    sysm = two_site(e, v, 0.0)
+    got = ow.propagate(sysm, np.array([[1.0], [0.0]]), t)[:, 0]
+    ref = np.exp(-1j * e * t) * np.array([np.cos(v * t), -1j * np.sin(v * t)])
+    assert np.abs(got - ref).max() < 1e-14
