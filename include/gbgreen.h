@@ -415,6 +415,32 @@ gb_status gb_add_sinv_terms(const gb_matrix* m, const gb_solve_params* p, double
 size_t gb_add_sinv_terms_workspace_size(const gb_matrix* m, const gb_solve_params* p);
 
 /*
+ * gb_wavepacket — propagate wavepackets by i S dc/dt = H c.
+ *
+ * The transport simulations of the paper propagate a hole wavepacket with a
+ * Schroedinger-type equation from an eigenstate such as the HOMO, with a step
+ * of ~0.1 fs (Quantum wavepacket dynamics).  Each of `nsteps` steps applies
+ * exp(-i tau S^-1 H) by its Chebyshev (Jacobi-Anger) series in
+ * A~ = (S^-1 H - b) / a, b, a the centre and half-width of [e_min, e_max]:
+ * one H product and one FP64 factor solve of S per term, the series cut where
+ * |J_k(a tau)| < 1e-17.
+ *   nwp       number of wavepackets (columns)
+ *   psi       device complex double [n][nwp] (re, im), in/out
+ *   tau       step in hbar / eV (0.1 fs = 0.15193 / eV)
+ *   e_min, e_max  bounds that contain every generalized eigenvalue of (H, S):
+ *             the series diverges outside them, so take them with a margin
+ *   nterms_out (host, may be NULL) receives the series length per step
+ *   workspace gb_wavepacket_workspace_size(m, nwp) bytes, 256-byte aligned
+ * GB_EINVAL without a factor (S's half-bandwidth above 63) or if a step needs
+ * more than 256 terms.  Synchronous.
+ */
+gb_status gb_wavepacket(const gb_matrix* m, int32_t nwp, void* psi, int32_t nsteps, double tau, double e_min,
+                        double e_max, int32_t* nterms_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of workspace gb_wavepacket needs (0: invalid arguments). */
+size_t gb_wavepacket_workspace_size(const gb_matrix* m, int32_t nwp);
+
+/*
  * gb_shifted_solve_batched — many independent systems in one persistent launch.
  *
  * The shifted equations of the Introduction for many independent structures

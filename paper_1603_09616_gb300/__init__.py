@@ -15,6 +15,7 @@ from ._binding import (  # noqa: F401
     add_sinv_terms,
     fermi_density,
     forces,
+    wavepacket,
     bsr_to_host,
     load,
     pattern_offsets,

@@ -42,6 +42,8 @@ EXPORTED = (
     "gb_fermi_density",
     "gb_correct_batched",
     "gb_forces",
+    "gb_wavepacket",
+    "gb_wavepacket_workspace_size",
     "gb_add_sinv_terms",
     "gb_add_sinv_terms_workspace_size",
     "gb_forces_workspace_size",
@@ -150,6 +152,11 @@ def load() -> C.CDLL:
                                       C.POINTER(Outputs), C.c_void_p, C.c_size_t, C.c_void_p]
     lib.gb_add_sinv_terms_workspace_size.restype = C.c_size_t
     lib.gb_add_sinv_terms_workspace_size.argtypes = [C.c_void_p, C.POINTER(SolveParams)]
+    lib.gb_wavepacket.restype = C.c_int
+    lib.gb_wavepacket.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                  C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.gb_wavepacket_workspace_size.restype = C.c_size_t
+    lib.gb_wavepacket_workspace_size.argtypes = [C.c_void_p, C.c_int32]
     lib.gb_forces.restype = C.c_int
     lib.gb_forces.argtypes = [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -511,6 +518,28 @@ def add_sinv_terms(mat: Matrix, cols, solved: dict, a_rho: float, b_edm: float, 
     _check(lib.gb_add_sinv_terms(mat.handle, C.byref(p), float(a_rho), float(b_edm), float(c_shs), C.byref(o),
                                  C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()), _stream_handle(stream)))
     return solved
+
+
+def wavepacket(mat: Matrix, psi, nsteps: int, tau: float, e_min: float, e_max: float, stream=None):
+    """Propagate the columns of ``psi`` (complex128 device tensor [n, w], in
+    place) by ``nsteps`` steps exp(-i tau S^-1 H) (gb_wavepacket); returns
+    (psi, terms per step)."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if psi.dtype != torch.complex128 or not psi.is_contiguous() or psi.dim() != 2:
+        raise ValueError("psi must be a contiguous complex128 [n, w] tensor")
+    lib = load()
+    nwp = int(psi.shape[1])
+    need = lib.gb_wavepacket_workspace_size(mat.handle, nwp)
+    if need == 0:
+        raise GBError(GB_EINVAL, lib.gb_last_error().decode())
+    ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+    nt = C.c_int32(0)
+    _check(lib.gb_wavepacket(mat.handle, nwp, C.c_void_p(psi.data_ptr()), int(nsteps), float(tau), float(e_min),
+                             float(e_max), C.byref(nt), C.c_void_p(ws.data_ptr()), C.c_size_t(ws.numel()),
+                             _stream_handle(stream)))
+    return psi, int(nt.value)
 
 
 def forces(mat: Matrix, cols, rho, edm, grad_h, grad_s, atom_off, stream=None):

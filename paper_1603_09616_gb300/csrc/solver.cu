@@ -2847,3 +2847,182 @@ gb_status gb_add_sinv_terms(const gb_matrix* m, const gb_solve_params* p, double
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ wavepacket propagation
+// i S dc/dt = H c (time in hbar / eV): the transport simulations propagate a
+// hole wavepacket with a Schroedinger-type equation (Quantum wavepacket
+// dynamics).  One step c <- exp(-i tau S^-1 H) c is a Chebyshev series: with
+// A = S^-1 H, spec(A) in [e_min, e_max], b = (e_max + e_min) / 2,
+// a = (e_max - e_min) / 2 and A~ = (A - b) / a, the Jacobi-Anger expansion
+//   exp(-i tau A) = e^{-i b tau} [J_0(a tau) + 2 sum_{k>=1} (-i)^k J_k(a tau) T_k(A~)]
+// with T_{k+1} = 2 A~ T_k - T_{k-1}.  Each term costs one H product and one
+// FP64 factor solve; the series stops where |J_k(a tau)| < 1e-17.  One team
+// per chunk of W wavepackets runs every step (persistent); W is the smallest
+// power of two that spreads the packets over the SMs (at most 32).
+namespace {
+
+constexpr int kWpMaxTerms = 256;
+
+__global__ void __launch_bounds__(gbk::TPB, 1)
+    wavepacket_kernel(const __grid_constant__ gbk::Args a, double2* __restrict__ psi, int nwp, int nsteps,
+                      const double2* __restrict__ coef, int nterms, double ca, double cb, double2 phase,
+                      char* __restrict__ scratch, size_t panel_bytes, int* __restrict__ status) {
+  __shared__ gbk::Smem sm;
+  extern __shared__ __align__(16) char dyn_smem[];
+  gbk::team_init(sm, dyn_smem);
+  const int W = a.W;  // columns per team (1 .. 32)
+  const int c0 = blockIdx.x * W, tid = threadIdx.x, n = a.m.n;
+  const size_t NW = (size_t)4 * a.m.nb * W;
+  char* base = scratch + (size_t)blockIdx.x * 7 * panel_bytes;
+  double2* P = reinterpret_cast<double2*>(base);
+  double2* Tm = reinterpret_cast<double2*>(base + panel_bytes);      // T_{k-1}
+  double2* Tk = reinterpret_cast<double2*>(base + 2 * panel_bytes);  // T_k
+  double2* Y = reinterpret_cast<double2*>(base + 3 * panel_bytes);
+  double2* HX = reinterpret_cast<double2*>(base + 4 * panel_bytes);
+  double2* t1 = reinterpret_cast<double2*>(base + 5 * panel_bytes);
+  double2* t2 = reinterpret_cast<double2*>(base + 6 * panel_bytes);
+  if (tid < gbk::WMAX) sm.act[tid] = (tid < W && c0 + tid < nwp) ? 1 : 0;
+  if (tid == 0) sm.inner_count = 0;
+  for (size_t e = tid; e < NW; e += gbk::TPB) {  // panel layout: row-major, W columns
+    const int row = (int)(e / W), l = (int)(e - (size_t)row * W);
+    P[e] = (row < n && c0 + l < nwp) ? psi[(size_t)row * nwp + c0 + l] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  auto cm = [](double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+  // Y <- S^-1 H X (ends with a barrier)
+  auto apply_a = [&](const double2* X) {
+    for (int it = tid; it < a.m.nb * W; it += gbk::TPB) {
+      const int I = it / W, l = it - I * W;
+      double2 acc[4];
+      gbk::bsr_row_d(a.m, a.m.hb, X, W, l, I, acc);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) HX[(size_t)(4 * I + r) * W + l] = acc[r];
+    }
+    __syncthreads();
+    gbk::bc_solve<double>(a, sm, HX, Y, t1, t2, dyn_smem);
+  };
+  for (int step = 0; step < nsteps; ++step) {
+    double2* tm = Tm;
+    double2* tk = Tk;
+    // T_0 = P, accumulate c_0 T_0 into P's replacement at the end (held in Tm / Tk roles)
+    for (size_t e = tid; e < NW; e += gbk::TPB) tm[e] = P[e];
+    __syncthreads();
+    apply_a(tm);  // Y = A T_0
+    for (size_t e = tid; e < NW; e += gbk::TPB) {  // T_1 = (A T_0 - b T_0) / a ; P <- c_0 T_0 + c_1 T_1
+      const double2 t0 = tm[e];
+      const double2 v = make_double2((Y[e].x - cb * t0.x) * ca, (Y[e].y - cb * t0.y) * ca);
+      tk[e] = v;
+      const double2 s0 = cm(coef[0], t0), s1 = cm(coef[1], v);
+      P[e] = make_double2(s0.x + s1.x, s0.y + s1.y);
+    }
+    __syncthreads();
+    for (int k = 2; k < nterms; ++k) {
+      apply_a(tk);  // Y = A T_{k-1}
+      const double2 ck = coef[k];
+      for (size_t e = tid; e < NW; e += gbk::TPB) {  // T_k = 2 (A T_{k-1} - b T_{k-1}) / a - T_{k-2}
+        const double2 t1v = tk[e], t0v = tm[e];
+        const double2 v = make_double2(2.0 * (Y[e].x - cb * t1v.x) * ca - t0v.x, 2.0 * (Y[e].y - cb * t1v.y) * ca - t0v.y);
+        tm[e] = v;  // the slot of T_{k-2} now holds T_k
+        const double2 s = cm(ck, v);
+        P[e] = make_double2(P[e].x + s.x, P[e].y + s.y);
+      }
+      __syncthreads();
+      double2* sw = tm;  // T_k becomes the current term
+      tm = tk;
+      tk = sw;
+    }
+    for (size_t e = tid; e < NW; e += gbk::TPB) P[e] = cm(phase, P[e]);  // e^{-i b tau}
+    __syncthreads();
+  }
+  for (size_t e = tid; e < NW; e += gbk::TPB) {
+    const int row = (int)(e / W), l = (int)(e - (size_t)row * W);
+    if (row < n && c0 + l < nwp) psi[(size_t)row * nwp + c0 + l] = P[e];
+  }
+  if (tid == 0 && sm.bc_fail) atomicOr(status, gbk::kStTimeout);
+}
+
+}  // namespace
+
+extern "C" {
+
+static int wp_width(const gb_matrix* m, int nwp) {
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+  int w = 1;
+  while (w < 32 && (nwp + w - 1) / w > nsm) w <<= 1;
+  return w;
+}
+
+size_t gb_wavepacket_workspace_size(const gb_matrix* m, int32_t nwp) {
+  clear_error();
+  if (!m || nwp < 1) {
+    fail(GB_EINVAL, "NULL matrix or no wavepackets");
+    return 0;
+  }
+  const int w = wp_width(m, nwp);
+  const size_t chunks = ((size_t)nwp + w - 1) / w, panel = align256(16 * 4 * (size_t)m->nb * w);
+  return align256(16 * (size_t)kWpMaxTerms) + 256 + chunks * 7 * panel;
+}
+
+gb_status gb_wavepacket(const gb_matrix* m, int32_t nwp, void* psi, int32_t nsteps, double tau, double e_min,
+                        double e_max, int32_t* nterms_out, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!m || !psi || nwp < 1 || nsteps < 0) return fail(GB_EINVAL, "NULL argument, no wavepackets or nsteps < 0");
+  if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
+  if (!(e_max > e_min) || !std::isfinite(e_min) || !std::isfinite(e_max) || !(tau > 0.0) || !std::isfinite(tau))
+    return fail(GB_EINVAL, "need e_min < e_max and tau > 0");
+  const double ca = 2.0 / (e_max - e_min), cb = 0.5 * (e_max + e_min), z = 0.5 * (e_max - e_min) * tau;
+  // Jacobi-Anger coefficients c_0 = J_0(z), c_k = 2 (-i)^k J_k(z) up to |J_k| < 1e-17 past k > z
+  std::vector<double2> coef;
+  for (int k = 0; k < kWpMaxTerms; ++k) {
+    const double j = std::cyl_bessel_j((double)k, z);
+    const double mag = k == 0 ? j : 2.0 * j;
+    const int r = k & 3;  // (-i)^k = 1, -i, -1, i
+    coef.push_back(r == 0 ? make_double2(mag, 0.0)
+                   : r == 1 ? make_double2(0.0, -mag)
+                   : r == 2 ? make_double2(-mag, 0.0)
+                            : make_double2(0.0, mag));
+    if (k >= 2 && k > z && std::fabs(j) < 1e-17) break;
+  }
+  if ((int)coef.size() >= kWpMaxTerms)
+    return fail(GB_EINVAL, "(e_max - e_min) tau / 2 = %g needs more than %d terms: take shorter steps", z, kWpMaxTerms);
+  const int nterms = (int)coef.size();
+  if (nterms_out) *nterms_out = nterms;
+  const size_t need = gb_wavepacket_workspace_size(m, nwp);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(GB_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < need) return fail(GB_ENOMEM, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+  int dev = 0;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(GB_EINVAL, "current device differs from the matrix's device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  double2* d_coef = reinterpret_cast<double2*>(w);
+  int* d_st = reinterpret_cast<int*>(w + align256(16 * (size_t)kWpMaxTerms));
+  char* scratch = w + align256(16 * (size_t)kWpMaxTerms) + 256;
+  const int wc = wp_width(m, nwp);
+  const size_t panel = align256(16 * 4 * (size_t)m->nb * wc);
+  const unsigned chunks = (unsigned)((nwp + wc - 1) / wc);
+  GB_CUDA(cudaMemcpyAsync(d_coef, coef.data(), 16 * (size_t)nterms, cudaMemcpyHostToDevice, s));
+  GB_CUDA(cudaMemsetAsync(d_st, 0, sizeof(int), s));
+  GB_CUDA(cudaMemsetAsync(scratch, 0, (size_t)chunks * 7 * panel, s));
+  gbk::Args a;
+  std::memset(&a, 0, sizeof a);
+  a.m = m->dm;
+  a.W = wc;
+  a.inner_bchol = 1;
+  a.bc_bw_alloc = m->dm.bf_bw;
+  const size_t dyn = gbk::dyn_layout(true, wc, true, 0, m->dm.bf_bw).bytes;
+  GB_CUDA(cudaFuncSetAttribute(wavepacket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  const double2 phase = make_double2(std::cos(cb * tau), -std::sin(cb * tau));
+  wavepacket_kernel<<<chunks, gbk::TPB, dyn, s>>>(a, static_cast<double2*>(psi), nwp, nsteps, d_coef, nterms, ca, cb,
+                                                   phase, scratch, panel, d_st);
+  GB_CUDA(cudaGetLastError());
+  int hst = 0;
+  GB_CUDA(cudaMemcpyAsync(&hst, d_st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CUDA(cudaStreamSynchronize(s));
+  if (hst & gbk::kStTimeout) return fail(GB_ETIMEOUT, "a bounded wait for a staged factor tile gave up");
+  return GB_OK;
+}
+
+}  // extern "C"
