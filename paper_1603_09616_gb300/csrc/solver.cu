@@ -36,6 +36,18 @@ static gb_status cuda_fail(cudaError_t e, const char* what) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Caller-owned device buffers are read and written with vector accesses of
+// their element size (complex doubles as 16-byte double2): a pointer off that
+// boundary is an error, found here instead of as a misaligned access.
+static bool misaligned(const void* p, size_t bytes) { return p && (reinterpret_cast<uintptr_t>(p) % bytes) != 0; }
+static gb_status check_outputs(const gb_outputs* o) {
+  if (misaligned(o->ldos, 8) || misaligned(o->rho, 8) || misaligned(o->edm, 8) || misaligned(o->q, 8) ||
+      misaligned(o->e_loc, 8) || misaligned(o->resid, 8) || misaligned(o->iters, 4) ||
+      misaligned(o->inner_iters, 4) || misaligned(o->col_status, 4) || misaligned(o->g_proj, 16))
+    return fail(GB_EINVAL, "an output is not aligned to its element (g_proj: 16 bytes)");
+  return GB_OK;
+}
+
 }  // namespace gb
 
 struct gb_matrix {
@@ -665,6 +677,8 @@ gb_status gb_spmm(const gb_matrix* m, int32_t which, gb_precision prec, int32_t 
   if (which != 0 && which != 1) return fail(GB_EINVAL, "which must be 0 (H) or 1 (S)");
   if (w < 1 || w > 64) return fail(GB_EINVAL, "w must be in [1, 64]");
   if (prec != GB_FP64 && prec != GB_MIXED) return fail(GB_EINVAL, "bad precision");
+  if (misaligned(x, prec == GB_FP64 ? 16 : 8) || misaligned(y, prec == GB_FP64 ? 16 : 8))
+    return fail(GB_EINVAL, "x and y must be aligned to their complex element (16 bytes FP64, 8 FP32)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t esz = prec == GB_FP64 ? 16 : 8;
   const int64_t n4 = 4 * m->nb;
@@ -954,6 +968,7 @@ gb_status gb_shifted_solve(const gb_matrix* m, const gb_solve_params* p, const g
                            size_t workspace_bytes, void* stream) {
   clear_error();
   if (!out) return fail(GB_EINVAL, "outputs is NULL");
+  if (check_outputs(out) != GB_OK) return GB_EINVAL;
   Plan pl;
   const bool want_g = out->g_proj != nullptr;
   gb_status st = make_plan(m, p, want_g, &pl);
@@ -1087,6 +1102,8 @@ gb_status gb_apply_sinv(const gb_matrix* m, gb_precision prec, int32_t w, const 
     return fail(GB_EINVAL, "w must be 1, 2, 4, 8, 16 or 32");
   if (prec != GB_FP64 && prec != GB_MIXED) return fail(GB_EINVAL, "bad precision");
   if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
+  if (misaligned(x, prec == GB_FP64 ? 16 : 8) || misaligned(y, prec == GB_FP64 ? 16 : 8))
+    return fail(GB_EINVAL, "x and y must be aligned to their complex element");
   int dev = 0;
   GB_CUDA(cudaGetDevice(&dev));
   if (dev != m->device) return fail(GB_EINVAL, "current device %d differs from the matrix's device %d", dev, m->device);
@@ -1505,6 +1522,8 @@ gb_status gb_fermi_density(const gb_matrix* m, const gb_solve_params* p, const d
                            void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   if (!m || !p || !g_proj || !ldos || !mu || !out) return fail(GB_EINVAL, "NULL argument");
+  if (misaligned(g_proj, 16) || misaligned(ldos, 8) || check_outputs(out) != GB_OK)
+    return fail(GB_EINVAL, "g_proj must be 16-byte aligned and every other array to its element");
   const int K = p->nshift, nrhs = p->nrhs;
   if (K < 2 || !p->z_re || !p->z_im) return fail(GB_EINVAL, "need at least two shifts");
   if (nrhs != m->n || !p->rhs_cols) return fail(GB_EINVAL, "the electron count needs every orbital solved (nrhs = n)");
@@ -1902,6 +1921,7 @@ gb_status gb_shifted_solve_static(const gb_matrix* m, const gb_solve_params* p, 
   clear_error();
   if (!out) return fail(GB_EINVAL, "outputs is NULL");
   if (!p) return fail(GB_EINVAL, "params is NULL");
+  if (check_outputs(out) != GB_OK) return GB_EINVAL;
   if (p->nrhs > kStaticMaxRhs) return fail(GB_EINVAL, "nrhs %d exceeds the static limit %d", p->nrhs, kStaticMaxRhs);
   Plan pl;
   const bool want_g = out->g_proj != nullptr;
@@ -2170,6 +2190,8 @@ gb_status gb_shifted_solve_batched(int32_t nsys, const gb_matrix* const* mats, c
                                    void* stream) {
   clear_error();
   if (!outs) return fail(GB_EINVAL, "outputs is NULL");
+  for (int i = 0; i < nsys; ++i)
+    if (check_outputs(&outs[i]) != GB_OK) return GB_EINVAL;
   BatchPlan bp;
   gb_status st = make_batch_plan(nsys, mats, params, outs, panel, &bp);
   if (st != GB_OK) return st;
@@ -2657,6 +2679,9 @@ gb_status gb_forces(const gb_matrix* m, const gb_solve_params* p, const double* 
                     double* forces, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   if (!m || !p || !rho || !edm || !grad_h || !grad_s || !atom_off || !forces) return fail(GB_EINVAL, "NULL argument");
+  if (misaligned(rho, 8) || misaligned(edm, 8) || misaligned(grad_h, 8) || misaligned(grad_s, 8) ||
+      misaligned(forces, 8))
+    return fail(GB_EINVAL, "arrays must be aligned to their element");
   const int n = (int)m->n, nrhs = p->nrhs;
   if (n_atoms < 1 || atom_off[0] != 0 || atom_off[n_atoms] != n)
     return fail(GB_EINVAL, "atom_off must run from 0 to n over n_atoms atoms");
@@ -2796,6 +2821,7 @@ gb_status gb_add_sinv_terms(const gb_matrix* m, const gb_solve_params* p, double
   clear_error();
   if (!m || !p || !out || !p->rhs_cols || p->nrhs < 1) return fail(GB_EINVAL, "NULL argument or no columns");
   if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
+  if (check_outputs(out) != GB_OK) return GB_EINVAL;
   const int nrhs = p->nrhs;
   for (int c = 0; c < nrhs; ++c)
     if (p->rhs_cols[c] < 0 || p->rhs_cols[c] >= m->n) return fail(GB_EINVAL, "rhs_cols[%d] out of range", c);
@@ -2968,6 +2994,7 @@ gb_status gb_wavepacket(const gb_matrix* m, int32_t nwp, void* psi, int32_t nste
                         double e_max, int32_t* nterms_out, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   if (!m || !psi || nwp < 1 || nsteps < 0) return fail(GB_EINVAL, "NULL argument, no wavepackets or nsteps < 0");
+  if (misaligned(psi, 16)) return fail(GB_EINVAL, "psi must be 16-byte aligned (complex double)");
   if (m->dm.bf_bw <= 0) return fail(GB_EINVAL, "no factor: S's half-bandwidth exceeds 63");
   if (!(e_max > e_min) || !std::isfinite(e_min) || !std::isfinite(e_max) || !(tau > 0.0) || !std::isfinite(tau))
     return fail(GB_EINVAL, "need e_min < e_max and tau > 0");
