@@ -28,6 +28,8 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     ordered on that stream.  Calls documented as synchronous wait for their
  *     own work before returning.
+ *   - Device arrays must sit on their element's boundary (complex double 16
+ *     bytes, double 8, float and int32 4); a misaligned array is GB_EINVAL.
  *   - The library never frees caller memory and never calls into PyTorch.
  */
 #ifndef GBGREEN_H
