@@ -278,3 +278,25 @@ def test_fp64_cg_inner_solve_still_matches(dev):
     cols = np.arange(0, system.n, 11, dtype=np.int32)
     out, ref = run_case(dev, system, z, cols, "fp64", 1e-12, 5000, panel=4, flags=4)
     check_outputs(out, ref, 1e-10)
+
+
+def test_misaligned_complex_double_buffers_are_rejected(dev):
+    # a complex-double array 8 bytes off its 16-byte boundary is GB_EINVAL
+    # before any launch (the kernels read it as 16-byte vectors)
+    import ctypes as C
+
+    system = chain_4orb(8, seed=1)
+    mat = gbg.Matrix(system)
+    lib = gbg._binding.load()
+    buf = torch.zeros(4 * system.n + 4, dtype=torch.float64, device=dev)
+    out = torch.zeros(2 * system.n, dtype=torch.complex128, device=dev)
+    st = lib.gb_spmm(mat.handle, 0, gbg._binding.GB_FP64, 1, C.c_void_p(buf.data_ptr() + 8),
+                     C.c_void_p(out.data_ptr()), None)
+    assert st == gbg._binding.GB_EINVAL
+    assert "aligned" in lib.gb_last_error().decode()
+    psi = C.c_void_p(buf.data_ptr() + 8)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    st = lib.gb_wavepacket(mat.handle, 1, psi, 1, 0.1, -10.0, 10.0, None, C.c_void_p(ws.data_ptr()),
+                           C.c_size_t(ws.numel()), None)
+    assert st == gbg._binding.GB_EINVAL
+    mat.close()
