@@ -6,13 +6,12 @@ history and evaluates the residual from H and S in FP64.
   * With an exact inner solve (the FP64 factor solve) the two agree to
     rounding at any iteration count: stopped early, far from convergence,
     they match pair by pair.
-  * Where the solve stalls above tol (here: the mixed path with H p as an
-    unrefined FP32 product), the check reports the failing pairs from the
-    true residual, marks their columns unconverged in the outputs, and the
-    FP64 correction solve then brings every pair to tol and the outputs to the
-    oracle.  (No configuration tried, with inexact inner solves or the FP32
-    product, gave an estimate below tol with a true residual above it: the two
-    agreed to three or more digits.)
+  * With H p as an unrefined FP32 product (flags bit 5) the estimate drifts
+    below the true residual: columns meet tol by the estimate while the true
+    residual misses it.  The check reports the failing pairs from the true
+    residual (written into resid), marks their columns unconverged in the
+    outputs, and the FP64 correction solve then brings every pair to tol and
+    the outputs to the oracle.
 """
 import numpy as np
 import pytest
@@ -51,10 +50,10 @@ def test_true_residual_equals_estimate_with_exact_inner_solve(maker, panel):
 
 def test_true_residual_check_drives_the_correction():
     # Mixed path with H p as an unrefined FP32 product (flags bit 5): the
-    # recurrence stalls near 1e-5, above tol 1e-8.  The FP64 check finds the
-    # same pairs failing by their true residual, marks exactly those columns,
-    # and the FP64 correction then brings every pair to tol and the outputs to
-    # the oracle.
+    # recursive estimate reaches tol 1e-8 while true residuals stay above 1e-6.
+    # The FP64 check writes the true residual into resid, marks exactly the
+    # columns that miss tol by it, and the FP64 correction then brings every
+    # pair to tol and the outputs to the oracle.
     torch.cuda.set_device(0)
     system = ppv_chain(3, seed=8)
     z = shift_grid(-10, 6, 32, 0.05)
