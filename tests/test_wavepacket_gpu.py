@@ -51,3 +51,22 @@ def test_wavepacket_rejects_bad_bounds_and_long_steps():
     with pytest.raises(gbg.GBError, match="EINVAL"):
         gbg.wavepacket(mat, psi, 1, 100.0, -40.0, 40.0)  # a tau = 4000: too many terms
     mat.close()
+
+
+def test_wavepacket_many_packets_share_teams():
+    # 300 packets: more than one per SM, so teams take two columns each (the
+    # panel width grows with the packet count); every packet must still match
+    torch.cuda.set_device(0)
+    system = ppv_chain(2, seed=2)
+    H, S = system.dense()
+    lam = sla.eigh(H, S, eigvals_only=True)
+    span = lam.max() - lam.min()
+    rng = np.random.default_rng(21)
+    c0 = rng.standard_normal((system.n, 300)) + 1j * rng.standard_normal((system.n, 300))
+    tau, steps = 0.1 / HBAR_EV_FS, 5
+    mat = gbg.Matrix(system)
+    psi = torch.from_numpy(np.ascontiguousarray(c0)).cuda()
+    psi, _ = gbg.wavepacket(mat, psi, steps, tau, lam.min() - 0.01 * span, lam.max() + 0.01 * span)
+    ref = owp.propagate(system, c0, steps * tau)
+    assert np.abs(psi.cpu().numpy() - ref).max() < 1e-10 * np.abs(ref).max()
+    mat.close()
