@@ -61,6 +61,10 @@ def test_true_residual_check_drives_the_correction():
     cols = np.arange(0, system.n, 13, dtype=np.int32)
     mat = gbg.Matrix(system)
     kw = dict(tol=1e-8, maxit=3000, prec="mixed", w_rho=w_rho, w_edm=w_edm, panel=4, flags=32)
+    # without the check the solve reports success: every pair meets tol by its estimate
+    plain = gbg.shifted_solve(mat, z, cols, raise_on=(), **kw)
+    assert plain["status"] == 0, plain["message"]
+    assert (plain["resid"].cpu().numpy() <= 1e-8).all()
     checked = gbg.shifted_solve(mat, z, cols, raise_on=(), verify=True, **kw)
     est = checked["resid"].cpu().numpy()
     true = checked["resid_true"].cpu().numpy()
