@@ -502,8 +502,9 @@ gb_status gb_tune_panel_batched(int32_t nsys, const gb_matrix* const* mats, cons
 /*
  * gb_shifted_solve_static — gb_shifted_solve without any allocation.
  *
- * The paper has no counterpart: this entry point exists for callers that may
- * not allocate once they run — an application whose device memory belongs to
+ * It solves the same generalized shifted equations (Introduction); the paper
+ * has no counterpart for the memory scheme: this entry point exists for
+ * callers that may not allocate once they run — an application whose device memory belongs to
  * another runtime's pool that already claims the whole GPU, or a
  * latency-critical loop where cudaMalloc's implicit device synchronisation is
  * not acceptable.  Same arguments and results as gb_shifted_solve (caller-owned
